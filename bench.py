@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark: Delta-matrix simulated annealing for the QAP on GB300.
+
+One step = one whole single-chain SA run of the measured workload: set-up
+(B', Delta_0, C0 -- step (a) of section 2.2), I iterations of the window
+scan + Delta update (steps (b)-(e)), and the result.  With --gpus N (torchrun)
+every rank runs an independent replica of the chain on its own GPU (a single
+chain does not shard), so work per GPU is fixed ("scaling": "weak").
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of the
+same workload: the full schedule at I/10 iterations, which has the same
+acceptance rate a(I) as the full-length run.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "n100": dict(N=100, I=10 ** 8, seed=1,
+                 desc="single chain, N=100, A and B symmetric uniform int [0,99], "
+                      "zero diagonal, random p0, geometric cooling "
+                      "T0=0.5*mean|Delta0|, Tf=1e-3*T0, I=1e8"),
+}
+SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 bytes
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="n100")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- #
+# CPU oracle legs (only place bench.py touches oracle/)
+# --------------------------------------------------------------------------- #
+def _oracle_sample(N: int, I: int, seed: int, q):
+    import oracle
+    from paper_1208_2675_gb300 import instances
+    A, B, p0 = instances.taixxa_like(N, seed)
+    c = oracle.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=I, seed=seed)
+    t = time.perf_counter()
+    c.run(I)
+    dt = time.perf_counter() - t
+    q.put((dt, c.state()["accepts"]))
+
+
+def oracle_sample_seconds(N: int, I: int, seed: int):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    pr = ctx.Process(target=_oracle_sample, args=(N, I, seed, q))
+    pr.start()
+    return pr, q
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# --------------------------------------------------------------------------- #
+# clocks
+# --------------------------------------------------------------------------- #
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- #
+# our arm
+# --------------------------------------------------------------------------- #
+def run_ours(args, rank: int, world: int, local_rank: int, dist):
+    import numpy as np
+    import torch
+    from paper_1208_2675_gb300 import instances, sa
+
+    wl = WORKLOADS[args.workload]
+    N, I, seed = wl["N"], wl["I"], wl["seed"]
+    M = N * (N - 1) // 2
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    sa.lib()
+
+    # CPU oracle baseline (rank 0, N=1): started first, runs beside the GPU work.
+    cpu_proc = None
+    I_sample = I // 10
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_proc, cpu_q = oracle_sample_seconds(N, I_sample, seed)
+
+    A, B, p0 = instances.taixxa_like(N, seed)
+    stream_id = rank  # independent replicas: own Philox stream per rank
+    kw = dict(t0=0.5, tf=1e-3, total_iters=I, seed=seed, stream_id=stream_id)
+    At, Bt, pt = (torch.from_numpy(x).to(dev) for x in (A, B, p0))
+    p_out = torch.zeros(N, dtype=torch.int32, device=dev)
+    c_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    a_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+    chunk = int(os.environ.get("QAPSA_CHUNK_ITERS", str(1 << 26)))
+    sa_launches = -(-I // chunk)
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        ev[0].record(stream)
+        h = sa.Chain.from_device(At, Bt, pt, stream=stream.cuda_stream, **kw)
+        ev[1].record(stream)
+        h.run_async(I)
+        ev[2].record(stream)
+        sa.qap_sa_result_device(h.h, p_out.data_ptr(), c_out.data_ptr(), a_out.data_ptr())
+        ev[3].record(stream)
+        ev[3].synchronize()
+        h.sync()
+        acc = int(a_out.item())
+        h.close()
+        return ev[0].elapsed_time(ev[3]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3, acc
+
+    for _ in range(args.warmup):
+        step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
+    clocks.start()
+    t_steps, t_sa, accs = [], [], []
+    for _ in range(args.steps):
+        a, b, c = step()
+        t_steps.append(a)
+        t_sa.append(b)
+        accs.append(c)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total = sum(t_steps)
+    if dist:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_max = float(t.item())
+    else:
+        total_max = total
+
+    # ---- end to end through the host-pointer API (pinned host buffers) ----
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    ph = torch.from_numpy(p0).pin_memory()
+    e2e_times = []
+    for k in range(max(1, min(args.steps, 3)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = sa.Chain(Ah.numpy(), Bh.numpy(), ph.numpy(), **kw)
+        h.run(I)
+        p_res, cost_res, acc_res = h.result()
+        dt = time.perf_counter() - t0
+        h.close()
+        if k:  # first one warms the host path
+            e2e_times.append(dt)
+    e2e_value = I / statistics.median(e2e_times)
+
+    if rank != 0:
+        return
+    acc_mean = statistics.mean(accs)
+    per_step = total_max / args.steps
+    value = world * args.steps * I / total_max
+    # roofline: sa_cta_kernel, algorithmic shared-memory bytes per step
+    bytes_step = acc_mean * (8 * M + 2 * N * N) + 4 * I
+    t_kernel = statistics.mean(t_sa)
+    achieved = bytes_step / t_kernel / 1e9
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak = SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6 / 1e9  # one SM
+    line = {
+        "metric": "sa_iterations_per_sec",
+        "value": value,
+        "unit": "iter/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": per_step * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic (seeded Taixxa-like instance)",
+        "config": {"workload": wl["desc"], "N": N, "I": I, "chains_per_gpu": 1,
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "delta_cell_updates_per_sec": world * acc_mean * M / per_step,
+        "accept_rate": acc_mean / I,
+        "sa_kernel_s_per_step": t_kernel,
+        "e2e": {"value": e2e_value, "unit": "iter/s",
+                "h2d_bytes_per_step": 2 * N * N * 4 + 4 * N,
+                "d2h_bytes_per_step": 4 * N + 8 + 8},
+        "gpu_launches": args.steps * (4 + sa_launches),
+        "roofline": {"bound": "smem", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": "one SM: 128 B/clk x median SM clock under load "
+                                   "(derived; the kernel runs on one CTA)",
+                     "frac_of_chip": achieved / (peak * 152)},
+        "clocks": clk,
+    }
+    if cpu_proc is not None:
+        cpu_proc.join()
+        dt, acc_cpu = cpu_q.get()
+        line["cpu_baseline"] = {
+            "value": I_sample / dt, "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"full schedule of the same N=100 instance at I={I_sample} "
+                      f"(a(I)={acc_cpu / I_sample:.4f} vs {acc_mean / I:.4f} at I={I}); "
+                      f"{dt:.1f} s on {cpu_model()}"}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- #
+# reference arm: the CPU oracle
+# --------------------------------------------------------------------------- #
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1208_2675_gb300 import instances
+    wl = WORKLOADS[args.workload]
+    N, seed = wl["N"], wl["seed"]
+    I = wl["I"] // 10
+    A, B, p0 = instances.taixxa_like(N, seed)
+
+    def step():
+        c = oracle.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=I, seed=seed)
+        t = time.perf_counter()
+        c.run(I)
+        return time.perf_counter() - t
+
+    for _ in range(args.warmup):
+        step()
+    ts = [step() for _ in range(args.steps)]
+    total = sum(ts)
+    value = args.steps * I / total
+    line = {
+        "metric": "sa_iterations_per_sec", "value": value, "unit": "iter/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded Taixxa-like instance)",
+        "config": {"workload": wl["desc"], "N": N, "I": wl["I"], "chains_per_gpu": 1,
+                   "parallelism": "single CPU thread"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                         "sample": f"full schedule of the same instance at I={I} per step"},
+        "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_ours(args, rank, world, local_rank, dist)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * qap_sa.h -- C ABI of libqapsa: Delta-matrix simulated annealing (SA) for the
+ * quadratic assignment problem (QAP) on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: G. Paul, "A GPU implementation of the Simulated Annealing Heuristic
+ * for the Quadratic Assignment Problem", arXiv:1208.2675.
+ *   - cost of an assignment p:            Eq. (1), section 1
+ *   - acceptance of a proposed swap:      Eq. (2), section 2.1
+ *   - the Delta-matrix loop (a)-(e):      section 2.2
+ *   - window ("subset") search, first accepted proposal in sequential order:
+ *                                         section 3 (ii)
+ *   - B' kept permuted for coalescing:    Eq. (3), section 3 (i)
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major N x N int32 (element (i,j) at index i*N + j).
+ *     A[i][j] is the flow between facilities i and j, B[x][y] the distance
+ *     between locations x and y; p[i] is the location of facility i.
+ *     Version 1 accepts the symmetric case with zero diagonals (the instance
+ *     family of section 4) and entries in [-127, 127].
+ *   - Unless a name ends in _device, pointers are HOST pointers; the library
+ *     copies what it needs and never keeps a caller pointer after returning.
+ *   - Return value: QAP_OK (0) or a negative QAP_E_* status; on error nothing
+ *     the caller owns has been written and *out handles are left NULL.
+ *   - A handle is not thread-safe; distinct handles are independent and may be
+ *     used from different threads.
+ *   - There is no CPU fallback: if no usable CUDA device is present every
+ *     create call returns QAP_E_CUDA.
+ */
+#ifndef QAP_SA_H
+#define QAP_SA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QAP_EXPORT __attribute__((visibility("default")))
+#else
+#define QAP_EXPORT
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define QAP_OK            0
+#define QAP_E_INVAL      (-1) /* null pointer; N < 2; p0 not a permutation;
+                                 A or B not symmetric or diagonal not zero;
+                                 T0 or Tf not finite and > 0; total_iters == 0 */
+#define QAP_E_RANGE      (-2) /* an entry outside [-127, 127]; the swap-cost
+                                 bound 8 N max|A| max|B| exceeds 2^31 - 1;
+                                 or it + iters > total_iters */
+#define QAP_E_NOMEM      (-3) /* device or host allocation failed */
+#define QAP_E_CUDA       (-4) /* a CUDA call failed (message via strerror) */
+#define QAP_E_TIMEOUT    (-5) /* a bounded device-side wait expired */
+#define QAP_E_STATE      (-6) /* the device reported an inconsistent state */
+#define QAP_E_UNSUPPORTED (-7) /* N larger than the largest supported tier */
+
+/* ---- cooling schedule ---------------------------------------------------- */
+/* Temperature T of Eq. (2) is lowered after every iteration (section 2.1) by
+ * the geometric law T(it) = T0 * alpha^it, alpha = (Tf / T0)^(1 / (I - 1)),
+ * it = 0 .. I - 1, evaluated bit-reproducibly as a product of per-byte tables
+ * built by repeated squaring of alpha (see qap_sa_temperature).              */
+#define QAP_T_RELATIVE 1u /* t0 multiplies mean |Delta_0| over the M pairs,
+                             tf multiplies T0; if every Delta_0 is zero t0 and
+                             tf are used as absolute temperatures */
+
+typedef struct qap_schedule {
+  double t0;            /* T0, or its multiplier with QAP_T_RELATIVE        */
+  double tf;            /* Tf, or its multiplier with QAP_T_RELATIVE        */
+  uint64_t total_iters; /* I: the schedule spans it = 0 .. I - 1 (>= 1)     */
+  uint32_t flags;       /* QAP_T_RELATIVE or 0                              */
+  uint32_t stream_id;   /* Philox counter word 2: the chain's random stream */
+} qap_schedule;
+
+/* ---- one chain ----------------------------------------------------------- */
+typedef struct qap_sa qap_sa; /* opaque; created by qap_sa_create*, freed by
+                                 qap_sa_destroy */
+
+/* Step (a) of section 2.2: copy A, B, p0 to the device, build B' (Eq. 3),
+ * the initial Delta for all M = N(N-1)/2 pairs r < s and the cost C0 of
+ * Eq. (1), then fix the schedule.  Random numbers: the r of Eq. (2) at
+ * iteration it is u = (x + 0.5) / 2^32 with x word (it mod 4) of
+ * Philox4x32-10(counter = (it/4 low, it/4 high, stream_id, 0),
+ * key = (seed low, seed high)).  Blocks until the set-up is done.
+ *   A, B  : host, N*N int32 each, row-major, symmetric, zero diagonal
+ *   N     : 2 .. qap_sa_max_n()
+ *   p0    : host, N int32, a permutation of 0 .. N-1
+ *   sched : host, read during the call only
+ *   out   : receives the new handle                                         */
+QAP_EXPORT int qap_sa_create(const int32_t *A, const int32_t *B, int32_t N,
+                  const int32_t *p0, const qap_schedule *sched, uint64_t seed,
+                  qap_sa **out);
+
+/* As qap_sa_create, but A, B and p0 are DEVICE pointers (same layouts) that
+ * must stay valid until this call returns, and all device work of the handle
+ * is issued on `cuda_stream` (a cudaStream_t; NULL = a stream the library
+ * creates and owns).  The caller's buffers are only read.                   */
+QAP_EXPORT int qap_sa_create_device(const int32_t *A, const int32_t *B, int32_t N,
+                         const int32_t *p0, const qap_schedule *sched,
+                         uint64_t seed, void *cuda_stream, qap_sa **out);
+
+/* Steps (b)-(d) of section 2.2 for exactly `iters` more iterations: proposals
+ * are the pairs r < s in row-major cyclic order, pair(it mod M); each is
+ * accepted by Eq. (2) (delta <= 0 always; otherwise iff
+ * (double)delta < -(T(it) * log(u)) in IEEE binary64); on acceptance p, the
+ * cost and Delta are updated.  Windows of consecutive proposals are tested in
+ * parallel and the first accepted one in sequential order is taken
+ * (section 3 (ii)), so the trajectory equals the sequential one.
+ * run(a); run(b) gives the same state as run(a + b).  Blocks until done.
+ * Returns QAP_E_RANGE if it + iters > total_iters.                          */
+QAP_EXPORT int qap_sa_run(qap_sa *h, uint64_t iters);
+
+/* As qap_sa_run but only enqueues the work on the handle's stream and
+ * returns; qap_sa_sync waits for it and reports device-side errors.         */
+QAP_EXPORT int qap_sa_run_async(qap_sa *h, uint64_t iters);
+QAP_EXPORT int qap_sa_sync(qap_sa *h);
+
+/* Current state after a stream sync: p (N int32, host), the int64 cost of
+ * Eq. (1) for p, and the number of accepted swaps.  Any output pointer may
+ * be NULL.                                                                  */
+QAP_EXPORT int qap_sa_result(qap_sa *h, int32_t *p_out, int64_t *cost,
+                  uint64_t *accepts);
+
+/* As qap_sa_result, into DEVICE buffers, enqueued on the handle's stream
+ * without a host sync.  Any output pointer may be NULL.                     */
+QAP_EXPORT int qap_sa_result_device(qap_sa *h, int32_t *p_out, int64_t *cost,
+                         uint64_t *accepts);
+
+/* Diagnostics of the current state (after a stream sync). */
+typedef struct qap_sa_info {
+  int32_t N;
+  int32_t tier;           /* 1 = one CTA with everything in shared memory   */
+  uint64_t iterations;    /* it: iterations done                            */
+  uint64_t accepts;
+  int64_t cost;
+  uint64_t near_ties;     /* evaluations with |delta + T ln u| < 1e-9 T     */
+  uint64_t exact_evals;   /* acceptance tests decided in binary64           */
+  uint64_t windows;       /* windows scanned                                */
+  double T0, Tf, alpha;   /* the schedule actually used                     */
+  uint64_t total_iters;
+  uint64_t smem_bytes;    /* dynamic shared memory of the SA kernel         */
+} qap_sa_info;
+QAP_EXPORT int qap_sa_get_info(qap_sa *h, qap_sa_info *out);
+
+/* The current Delta (after a stream sync) as M int32 values in pair order
+ * (r < s, row-major): delta_out[m] is the cost change of swapping pair(m).  */
+QAP_EXPORT int qap_sa_delta(qap_sa *h, int32_t *delta_out);
+
+/* T(it) of the handle's schedule as a binary64 (see qap_schedule).          */
+QAP_EXPORT double qap_sa_temperature(const qap_sa *h, uint64_t it);
+
+/* Frees every resource of the handle (NULL is ignored).                     */
+QAP_EXPORT void qap_sa_destroy(qap_sa *h);
+
+/* ---- library ------------------------------------------------------------- */
+/* Largest N any tier supports on the current device (0 if no device).       */
+QAP_EXPORT int32_t qap_sa_max_n(void);
+
+/* Static text for a status code; for QAP_E_CUDA the last CUDA error text of
+ * the calling thread is appended.                                            */
+QAP_EXPORT const char *qap_sa_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QAP_SA_H */

@@ -1,0 +1,457 @@
+// qap_sa.cu -- host runtime of libqapsa: the C ABI declared in
+// include/qap_sa.h.  Validates inputs, owns device memory and streams, fixes
+// the cooling schedule, and launches the kernels of sa_kernels.cuh.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "qap_sa.h"
+#include "sa_kernels.cuh"
+
+using namespace qapsa;
+
+namespace {
+
+thread_local char g_errbuf[256];
+
+int cuda_fail(cudaError_t e, const char *what) {
+  snprintf(g_errbuf, sizeof g_errbuf, "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? QAP_E_NOMEM : QAP_E_CUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// Iterations per launch of the SA kernel: bounds the length of one kernel and
+// lets the host see device errors between launches.  run(a); run(b) equals
+// run(a + b), so the split does not change the trajectory.
+unsigned long long chunk_iters() {
+  static unsigned long long v = [] {
+    const char *e = getenv("QAPSA_CHUNK_ITERS");
+    unsigned long long x = e ? strtoull(e, nullptr, 10) : 0ull;
+    return x ? x : (1ull << 26);
+  }();
+  return v;
+}
+
+int device_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+      cudaSuccess)
+    return 0;
+  return v;
+}
+
+// Row stride of the int8 A and B' rows: a whole number of 32-bit words, odd
+// so that threads reading different rows at the same word hit distinct banks.
+int row_stride(int N) {
+  int w = (N + 3) / 4;
+  if ((w & 1) == 0) ++w;
+  return 4 * w;
+}
+
+int pow2_floor(int x) {
+  int p = 1;
+  while (p * 2 <= x) p *= 2;
+  return p;
+}
+
+// The cooling schedule, built exactly as the header documents it.
+struct Schedule {
+  double T0, Tf, alpha;
+  unsigned long long I;
+  double P[8][256];
+};
+
+void build_schedule(Schedule *S, double T0, double Tf, unsigned long long I) {
+  S->T0 = T0;
+  S->Tf = Tf;
+  S->I = I;
+  const double ratio = Tf / T0;
+  S->alpha = (I >= 2) ? pow(ratio, 1.0 / (double)(I - 1)) : 1.0;
+  double sq[64];
+  sq[0] = S->alpha;
+  for (int i = 1; i < 64; ++i) sq[i] = sq[i - 1] * sq[i - 1];
+  for (int b = 0; b < 8; ++b)
+    for (int v = 0; v < 256; ++v) {
+      double f = 1.0;
+      for (int bit = 0; bit < 8; ++bit)
+        if (v & (1 << bit)) f = f * sq[8 * b + bit];
+      S->P[b][v] = f;
+    }
+}
+
+double schedule_T(const Schedule &S, unsigned long long it) {
+  double T = S.T0;
+  for (int b = 7; b >= 0; --b) T = T * S.P[b][(it >> (8 * b)) & 255u];
+  return T;
+}
+
+}  // namespace
+
+struct qap_sa {
+  int N = 0, S = 0, M = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int8_t *A8 = nullptr, *Bp8 = nullptr;
+  int *delta = nullptr, *p = nullptr, *d = nullptr;
+  ChainStatus *st = nullptr;
+  double *P = nullptr;
+  Schedule sched;
+  ChainDev dev{};
+  SmemLayout layout{};
+  unsigned long long it_host = 0;  // iterations enqueued so far
+  int tier = 1;
+};
+
+namespace {
+
+void free_handle(qap_sa *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  cudaFree(h->A8);
+  cudaFree(h->Bp8);
+  cudaFree(h->delta);
+  cudaFree(h->p);
+  cudaFree(h->d);
+  cudaFree(h->st);
+  cudaFree(h->P);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int tier1_fits(int N) {
+  const int S = row_stride(N);
+  const int M = N * (N - 1) / 2;
+  return smem_layout(N, S, M).bytes <= device_smem_optin();
+}
+
+int max_n_tier1() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  int lo = 2, hi = 1024;
+  if (!tier1_fits(lo)) return 0;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) / 2;
+    if (tier1_fits(mid)) lo = mid; else hi = mid - 1;
+  }
+  cached = lo;
+  return lo;
+}
+
+// Common body of the two create entry points; A32/B32/p032 are device
+// pointers that stay valid for the duration of the call.
+int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
+                  const int32_t *p032, const qap_schedule *sc, uint64_t seed,
+                  cudaStream_t stream, bool own_stream, qap_sa **out) {
+  qap_sa *h = new (std::nothrow) qap_sa();
+  if (!h) return QAP_E_NOMEM;
+  h->N = N;
+  h->S = row_stride(N);
+  h->M = N * (N - 1) / 2;
+  h->stream = stream;
+  h->own_stream = own_stream;
+  const int S = h->S, M = h->M;
+  int rc = QAP_OK;
+  int *count = nullptr, *G = nullptr;
+  SetupOut *so = nullptr;
+  SetupOut so_h{};
+  auto fail = [&](int code) {
+    cudaFree(count);
+    cudaFree(G);
+    cudaFree(so);
+    free_handle(h);
+    return code;
+  };
+#define CKF(call)                                           \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call)); \
+  } while (0)
+  const size_t nS = (size_t)N * S;
+  CKF(cudaMalloc(&h->A8, nS));
+  CKF(cudaMalloc(&h->Bp8, nS));
+  CKF(cudaMalloc(&h->delta, sizeof(int) * (size_t)(M > 0 ? M : 1)));
+  CKF(cudaMalloc(&h->p, sizeof(int) * N));
+  CKF(cudaMalloc(&h->d, sizeof(int) * N));
+  CKF(cudaMalloc(&h->st, sizeof(ChainStatus)));
+  CKF(cudaMalloc(&h->P, sizeof(double) * 8 * 256));
+  CKF(cudaMalloc(&count, sizeof(int) * N));
+  CKF(cudaMalloc(&G, sizeof(int) * (size_t)N * N));
+  CKF(cudaMalloc(&so, sizeof(SetupOut)));
+  CKF(cudaMemsetAsync(h->A8, 0, nS, stream));
+  CKF(cudaMemsetAsync(h->Bp8, 0, nS, stream));
+  CKF(cudaMemsetAsync(count, 0, sizeof(int) * N, stream));
+  CKF(cudaMemsetAsync(so, 0, sizeof(SetupOut), stream));
+  CKF(cudaMemsetAsync(h->st, 0, sizeof(ChainStatus), stream));
+  {
+    const long long NN = (long long)N * N;
+    const int blocks = (int)((NN + 255) / 256 < 4096 ? (NN + 255) / 256 : 4096);
+    setup_pack_kernel<<<blocks, 256, 0, stream>>>(A32, B32, p032, N, S, h->A8,
+                                                  count, so);
+    setup_bprime_kernel<<<blocks, 256, 0, stream>>>(B32, p032, N, S, count,
+                                                    h->Bp8, h->p, so);
+    dim3 gg((N + 127) / 128, N);
+    setup_gram_kernel<<<gg, 128, 0, stream>>>(h->A8, h->Bp8, N, S, G);
+    setup_delta_kernel<<<gg, 128, 0, stream>>>(G, h->A8, h->Bp8, N, S,
+                                               h->delta, h->d, so);
+    CKF(cudaGetLastError());
+  }
+  CKF(cudaMemcpyAsync(&so_h, so, sizeof so_h, cudaMemcpyDeviceToHost, stream));
+  CKF(cudaStreamSynchronize(stream));
+  cudaFree(count);
+  count = nullptr;
+  cudaFree(G);
+  G = nullptr;
+  cudaFree(so);
+  so = nullptr;
+  if (so_h.flags & (kFlagAsym | kFlagDiag | kFlagPerm)) return fail(QAP_E_INVAL);
+  if (so_h.flags & (kFlagRangeA | kFlagRangeB)) return fail(QAP_E_RANGE);
+  // Swap costs and the intermediate sums of the rows-r,s recompute stay
+  // below 8 N max|A| max|B| in magnitude; all must fit in int32.
+  if (8.0 * N * (double)so_h.max_abs_a * (double)so_h.max_abs_b > 2147483647.0)
+    return fail(QAP_E_RANGE);
+
+  // ---- schedule ----
+  double T0 = sc->t0, Tf = sc->tf;
+  if (sc->flags & QAP_T_RELATIVE) {
+    const double mean = so_h.sum_abs_delta > 0
+                            ? (double)so_h.sum_abs_delta / (double)M
+                            : 1.0;
+    T0 = sc->t0 * mean;
+    Tf = sc->tf * T0;
+  }
+  if (!(T0 > 0.0) || !(Tf > 0.0) || !isfinite(T0) || !isfinite(Tf))
+    return fail(QAP_E_INVAL);
+  build_schedule(&h->sched, T0, Tf, sc->total_iters);
+  CKF(cudaMemcpyAsync(h->P, h->sched.P, sizeof h->sched.P,
+                      cudaMemcpyHostToDevice, stream));
+  {
+    ChainStatus st0{};
+    st0.cost = so_h.cost0;
+    CKF(cudaMemcpyAsync(h->st, &st0, sizeof st0, cudaMemcpyHostToDevice,
+                        stream));
+  }
+  ChainDev &g = h->dev;
+  g.N = N;
+  g.S = S;
+  g.M = M;
+  g.tpv = N <= 32 ? 32 : pow2_floor(kThreads / N);
+  if (g.tpv > 32) g.tpv = 32;
+  g.A = h->A8;
+  g.Bp = h->Bp8;
+  g.delta = h->delta;
+  g.p = h->p;
+  g.d = h->d;
+  g.st = h->st;
+  g.seed = seed;
+  g.stream = sc->stream_id;
+  g.T0 = T0;
+  g.P = h->P;
+  g.T0f = (float)T0;
+  const double l2r = log2(Tf / T0);
+  g.log2a_f = sc->total_iters >= 2 ? (float)(l2r / (double)(sc->total_iters - 1)) : 0.0f;
+  // Pre-test margin: covers binary32 rounding of T and -ln u, the byte-table
+  // product's drift from T0 alpha^it, and the exponent's rounding.
+  g.mrel = (float)(2e-5 + 2e-7 * fabs(l2r) + 8.0 * (double)sc->total_iters * 0x1p-53);
+  h->layout = smem_layout(N, S, M);
+  CKF(cudaFuncSetAttribute(sa_cta_kernel,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           h->layout.bytes));
+  CKF(cudaStreamSynchronize(stream));
+  *out = h;
+  return rc;
+#undef CKF
+}
+
+int validate_args(const void *A, const void *B, int32_t N, const void *p0,
+                  const qap_schedule *sc, qap_sa **out) {
+  if (!out) return QAP_E_INVAL;
+  *out = nullptr;
+  if (!A || !B || !p0 || !sc) return QAP_E_INVAL;
+  if (N < 2) return QAP_E_INVAL;
+  if (sc->total_iters == 0) return QAP_E_INVAL;
+  if (!(sc->t0 > 0.0) || !(sc->tf > 0.0) || !isfinite(sc->t0) || !isfinite(sc->tf))
+    return QAP_E_INVAL;
+  if (sc->flags & ~QAP_T_RELATIVE) return QAP_E_INVAL;
+  const int nmax = max_n_tier1();
+  if (nmax == 0) return QAP_E_CUDA;
+  if (N > nmax) return QAP_E_UNSUPPORTED;
+  return QAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qap_sa_create(const int32_t *A, const int32_t *B, int32_t N,
+                  const int32_t *p0, const qap_schedule *sched, uint64_t seed,
+                  qap_sa **out) {
+  int rc = validate_args(A, B, N, p0, sched, out);
+  if (rc) return rc;
+  cudaStream_t st = nullptr;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  int32_t *dA = nullptr, *dB = nullptr, *dp = nullptr;
+  const size_t nn = sizeof(int32_t) * (size_t)N * N;
+  cudaError_t e = cudaMalloc(&dA, nn);
+  if (e == cudaSuccess) e = cudaMalloc(&dB, nn);
+  if (e == cudaSuccess) e = cudaMalloc(&dp, sizeof(int32_t) * N);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dA, A, nn, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dB, B, nn, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dp, p0, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "staging copy");
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dp);
+    cudaStreamDestroy(st);
+    return rc;
+  }
+  // create_common synchronises the stream before it returns, and on failure
+  // destroys it together with the partial handle.
+  rc = create_common(dA, dB, N, dp, sched, seed, st, true, out);
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dp);
+  return rc;  // on failure create_common destroyed the stream with the handle
+}
+
+int qap_sa_create_device(const int32_t *A, const int32_t *B, int32_t N,
+                         const int32_t *p0, const qap_schedule *sched,
+                         uint64_t seed, void *cuda_stream, qap_sa **out) {
+  int rc = validate_args(A, B, N, p0, sched, out);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  bool own = false;
+  if (!st) {
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    own = true;
+  }
+  return create_common(A, B, N, p0, sched, seed, st, own, out);
+}
+
+int qap_sa_run_async(qap_sa *h, uint64_t iters) {
+  if (!h) return QAP_E_INVAL;
+  if (iters > h->sched.I || h->it_host + iters > h->sched.I) return QAP_E_RANGE;
+  const unsigned long long end = h->it_host + iters;
+  unsigned long long cur = h->it_host;
+  while (cur < end) {
+    unsigned long long stop = cur + chunk_iters();
+    if (stop > end) stop = end;
+    sa_cta_kernel<<<1, kThreads, h->layout.bytes, h->stream>>>(h->dev, stop);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "sa_cta_kernel launch");
+    cur = stop;
+  }
+  h->it_host = end;
+  return QAP_OK;
+}
+
+int qap_sa_sync(qap_sa *h) {
+  if (!h) return QAP_E_INVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  int err = 0;
+  CK(cudaMemcpy(&err, &h->st->error, sizeof err, cudaMemcpyDeviceToHost));
+  return err ? QAP_E_STATE : QAP_OK;
+}
+
+int qap_sa_run(qap_sa *h, uint64_t iters) {
+  int rc = qap_sa_run_async(h, iters);
+  if (rc) return rc;
+  return qap_sa_sync(h);
+}
+
+int qap_sa_result(qap_sa *h, int32_t *p_out, int64_t *cost,
+                  uint64_t *accepts) {
+  if (!h) return QAP_E_INVAL;
+  ChainStatus st{};
+  CK(cudaMemcpyAsync(&st, h->st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+  if (p_out)
+    CK(cudaMemcpyAsync(p_out, h->p, sizeof(int32_t) * h->N,
+                       cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st.error) return QAP_E_STATE;
+  if (cost) *cost = st.cost;
+  if (accepts) *accepts = st.accepts;
+  return QAP_OK;
+}
+
+int qap_sa_result_device(qap_sa *h, int32_t *p_out, int64_t *cost,
+                         uint64_t *accepts) {
+  if (!h) return QAP_E_INVAL;
+  if (p_out)
+    CK(cudaMemcpyAsync(p_out, h->p, sizeof(int32_t) * h->N,
+                       cudaMemcpyDeviceToDevice, h->stream));
+  if (cost)
+    CK(cudaMemcpyAsync(cost, &h->st->cost, sizeof(int64_t),
+                       cudaMemcpyDeviceToDevice, h->stream));
+  if (accepts)
+    CK(cudaMemcpyAsync(accepts, &h->st->accepts, sizeof(uint64_t),
+                       cudaMemcpyDeviceToDevice, h->stream));
+  return QAP_OK;
+}
+
+int qap_sa_get_info(qap_sa *h, qap_sa_info *out) {
+  if (!h || !out) return QAP_E_INVAL;
+  ChainStatus st{};
+  CK(cudaMemcpyAsync(&st, h->st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  memset(out, 0, sizeof *out);
+  out->N = h->N;
+  out->tier = h->tier;
+  out->iterations = st.it;
+  out->accepts = st.accepts;
+  out->cost = st.cost;
+  out->near_ties = st.near_ties;
+  out->exact_evals = st.exact_evals;
+  out->windows = st.windows;
+  out->T0 = h->sched.T0;
+  out->Tf = h->sched.Tf;
+  out->alpha = h->sched.alpha;
+  out->total_iters = h->sched.I;
+  out->smem_bytes = (uint64_t)h->layout.bytes;
+  return st.error ? QAP_E_STATE : QAP_OK;
+}
+
+int qap_sa_delta(qap_sa *h, int32_t *delta_out) {
+  if (!h || !delta_out) return QAP_E_INVAL;
+  CK(cudaMemcpyAsync(delta_out, h->delta, sizeof(int32_t) * (size_t)h->M,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return QAP_OK;
+}
+
+double qap_sa_temperature(const qap_sa *h, uint64_t it) {
+  if (!h) return 0.0;
+  return schedule_T(h->sched, it);
+}
+
+void qap_sa_destroy(qap_sa *h) { free_handle(h); }
+
+int32_t qap_sa_max_n(void) { return max_n_tier1(); }
+
+const char *qap_sa_strerror(int status) {
+  switch (status) {
+    case QAP_OK: return "ok";
+    case QAP_E_INVAL: return "invalid argument";
+    case QAP_E_RANGE: return "value out of range";
+    case QAP_E_NOMEM: return "out of memory";
+    case QAP_E_CUDA: return g_errbuf[0] ? g_errbuf : "CUDA error";
+    case QAP_E_TIMEOUT: return "device wait timed out";
+    case QAP_E_STATE: return "inconsistent device state";
+    case QAP_E_UNSUPPORTED: return "problem size not supported";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+"""ctypes binding of libqapsa (include/qap_sa.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; all of the
+annealing runs in the CUDA kernels of the library. If ``libqapsa.so`` has not
+been built, or no CUDA device is usable, calls raise -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqapsa.so")
+
+QAP_OK = 0
+QAP_E_INVAL = -1
+QAP_E_RANGE = -2
+QAP_E_NOMEM = -3
+QAP_E_CUDA = -4
+QAP_E_TIMEOUT = -5
+QAP_E_STATE = -6
+QAP_E_UNSUPPORTED = -7
+QAP_T_RELATIVE = 1
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+
+class qap_schedule(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_double), ("tf", ctypes.c_double),
+                ("total_iters", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("stream_id", ctypes.c_uint32)]
+
+
+class qap_sa_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("tier", ctypes.c_int32),
+                ("iterations", ctypes.c_uint64), ("accepts", ctypes.c_uint64),
+                ("cost", ctypes.c_int64), ("near_ties", ctypes.c_uint64),
+                ("exact_evals", ctypes.c_uint64), ("windows", ctypes.c_uint64),
+                ("T0", ctypes.c_double), ("Tf", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("total_iters", ctypes.c_uint64),
+                ("smem_bytes", ctypes.c_uint64)]
+
+
+# Every symbol include/qap_sa.h declares, with its ctypes signature.
+SIGNATURES = {
+    "qap_sa_create": (ctypes.c_int, [_i32p, _i32p, ctypes.c_int32, _i32p,
+                                     ctypes.POINTER(qap_schedule), ctypes.c_uint64,
+                                     ctypes.POINTER(ctypes.c_void_p)]),
+    "qap_sa_create_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.POINTER(qap_schedule),
+                                            ctypes.c_uint64, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_void_p)]),
+    "qap_sa_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "qap_sa_run_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "qap_sa_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "qap_sa_result": (ctypes.c_int, [ctypes.c_void_p, _i32p, _i64p, _u64p]),
+    "qap_sa_result_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "qap_sa_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qap_sa_info)]),
+    "qap_sa_delta": (ctypes.c_int, [ctypes.c_void_p, _i32p]),
+    "qap_sa_temperature": (ctypes.c_double, [ctypes.c_void_p, ctypes.c_uint64]),
+    "qap_sa_destroy": (None, [ctypes.c_void_p]),
+    "qap_sa_max_n": (ctypes.c_int32, []),
+    "qap_sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libqapsa.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class QapError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().qap_sa_strerror(status).decode()
+        super().__init__(f"{where}: status {status} ({msg})")
+
+
+def _check(status: int, where: str) -> None:
+    if status != QAP_OK:
+        raise QapError(status, where)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def make_schedule(t0: float, tf: float, total_iters: int, relative: bool = True,
+                  stream_id: int = 0) -> qap_schedule:
+    return qap_schedule(float(t0), float(tf), int(total_iters),
+                        QAP_T_RELATIVE if relative else 0, int(stream_id))
+
+
+# ---- C entry points, same names ------------------------------------------- #
+def qap_sa_create(A, B, p0, sched: qap_schedule, seed: int) -> ctypes.c_void_p:
+    A, B, p0 = _i32(A), _i32(B), _i32(p0)
+    h = ctypes.c_void_p()
+    _check(lib().qap_sa_create(A.ctypes.data_as(_i32p), B.ctypes.data_as(_i32p),
+                               len(p0), p0.ctypes.data_as(_i32p), ctypes.byref(sched),
+                               int(seed), ctypes.byref(h)), "qap_sa_create")
+    return h
+
+
+def qap_sa_create_device(A_ptr: int, B_ptr: int, N: int, p0_ptr: int,
+                         sched: qap_schedule, seed: int, stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().qap_sa_create_device(ctypes.c_void_p(A_ptr), ctypes.c_void_p(B_ptr),
+                                      int(N), ctypes.c_void_p(p0_ptr), ctypes.byref(sched),
+                                      int(seed), ctypes.c_void_p(stream or None),
+                                      ctypes.byref(h)), "qap_sa_create_device")
+    return h
+
+
+def qap_sa_run(h, iters: int) -> None:
+    _check(lib().qap_sa_run(h, int(iters)), "qap_sa_run")
+
+
+def qap_sa_run_async(h, iters: int) -> None:
+    _check(lib().qap_sa_run_async(h, int(iters)), "qap_sa_run_async")
+
+
+def qap_sa_sync(h) -> None:
+    _check(lib().qap_sa_sync(h), "qap_sa_sync")
+
+
+def qap_sa_result(h, N: int):
+    p = np.zeros(N, dtype=np.int32)
+    cost = ctypes.c_int64()
+    acc = ctypes.c_uint64()
+    _check(lib().qap_sa_result(h, p.ctypes.data_as(_i32p), ctypes.byref(cost),
+                               ctypes.byref(acc)), "qap_sa_result")
+    return p, cost.value, acc.value
+
+
+def qap_sa_result_device(h, p_ptr: int, cost_ptr: int, acc_ptr: int) -> None:
+    _check(lib().qap_sa_result_device(h, ctypes.c_void_p(p_ptr or None),
+                                      ctypes.c_void_p(cost_ptr or None),
+                                      ctypes.c_void_p(acc_ptr or None)),
+           "qap_sa_result_device")
+
+
+def qap_sa_get_info(h) -> dict:
+    info = qap_sa_info()
+    _check(lib().qap_sa_get_info(h, ctypes.byref(info)), "qap_sa_get_info")
+    return {name: getattr(info, name) for name, _ in qap_sa_info._fields_}
+
+
+def qap_sa_delta(h, M: int) -> np.ndarray:
+    out = np.zeros(max(M, 1), dtype=np.int32)
+    _check(lib().qap_sa_delta(h, out.ctypes.data_as(_i32p)), "qap_sa_delta")
+    return out[:M]
+
+
+def qap_sa_temperature(h, it: int) -> float:
+    return float(lib().qap_sa_temperature(h, int(it)))
+
+
+def qap_sa_destroy(h) -> None:
+    if h:
+        lib().qap_sa_destroy(h)
+
+
+def qap_sa_max_n() -> int:
+    return int(lib().qap_sa_max_n())
+
+
+def qap_sa_strerror(status: int) -> str:
+    return lib().qap_sa_strerror(int(status)).decode()
+
+
+# ---- convenience wrapper ----------------------------------------------------- #
+class Chain:
+    """One SA chain on the GPU (a qap_sa handle)."""
+
+    def __init__(self, A, B, p0, *, t0: float, tf: float, total_iters: int,
+                 relative: bool = True, seed: int = 0, stream_id: int = 0):
+        self.N = len(p0)
+        self.M = self.N * (self.N - 1) // 2
+        self.sched = make_schedule(t0, tf, total_iters, relative, stream_id)
+        self.h = qap_sa_create(A, B, p0, self.sched, seed)
+
+    @classmethod
+    def from_device(cls, A_t, B_t, p0_t, *, t0: float, tf: float, total_iters: int,
+                    relative: bool = True, seed: int = 0, stream_id: int = 0,
+                    stream: int = 0) -> "Chain":
+        """A_t, B_t, p0_t: contiguous int32 CUDA tensors (any object with
+        data_ptr()); `stream` is a raw cudaStream_t (0 = library-owned)."""
+        self = cls.__new__(cls)
+        self.N = int(p0_t.shape[0])
+        self.M = self.N * (self.N - 1) // 2
+        self.sched = make_schedule(t0, tf, total_iters, relative, stream_id)
+        self.h = qap_sa_create_device(A_t.data_ptr(), B_t.data_ptr(), self.N,
+                                      p0_t.data_ptr(), self.sched, seed, stream)
+        return self
+
+    def run(self, iters: int) -> None:
+        qap_sa_run(self.h, iters)
+
+    def run_async(self, iters: int) -> None:
+        qap_sa_run_async(self.h, iters)
+
+    def sync(self) -> None:
+        qap_sa_sync(self.h)
+
+    def result(self):
+        return qap_sa_result(self.h, self.N)
+
+    def info(self) -> dict:
+        return qap_sa_get_info(self.h)
+
+    def delta(self) -> np.ndarray:
+        return qap_sa_delta(self.h, self.M)
+
+    def temperature(self, it: int) -> float:
+        return qap_sa_temperature(self.h, it)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            qap_sa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,228 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+The bar is bit-exact: Delta (int32 vs the oracle's int64), the permutation, the
+int64 cost, the accept count and the binary64 schedule must be identical, and
+both sides must report zero near-ties (|delta + T ln u| < 1e-9 T) -- a flip of
+the Eq. (2) decision between CUDA's and libm's log could only happen there.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_2675_gb300 import instances
+from paper_1208_2675_gb300 import sa
+
+pytestmark = pytest.mark.gpu
+
+
+def packed_upper(D):
+    N = D.shape[0]
+    return D[np.triu_indices(N, 1)]
+
+
+def run_both(A, B, p0, *, t0, tf, I, relative=True, seed=0, stream=0, splits=None,
+             oracle_iters=None):
+    """Runs I iterations (or oracle_iters of them) on both sides; returns
+    (gpu_state, oracle_state, gpu_delta_packed, oracle_delta_packed)."""
+    n_run = I if oracle_iters is None else oracle_iters
+    g = sa.Chain(A, B, p0, t0=t0, tf=tf, total_iters=I, relative=relative,
+                 seed=seed, stream_id=stream)
+    o = oracle.Chain(A, B, p0, t0=t0, tf=tf, total_iters=I, relative=relative,
+                     seed=seed, stream=stream)
+    if splits:
+        done = 0
+        for k in splits:
+            g.run(k)
+            done += k
+        assert done == n_run
+    else:
+        g.run(n_run)
+    o.run(n_run)
+    p, cost, acc = g.result()
+    info = g.info()
+    gs = {"p": p, "cost": cost, "accepts": acc, "it": info["iterations"],
+          "near_ties": info["near_ties"], "info": info}
+    out = (gs, o.state(), g.delta(), packed_upper(o.delta()), g, o)
+    return out
+
+
+def assert_same(gs, os_, gd, od):
+    assert gs["it"] == os_["it"]
+    assert gs["accepts"] == os_["accepts"]
+    assert gs["cost"] == os_["cost"]
+    assert np.array_equal(gs["p"], os_["p"])
+    assert np.array_equal(gd.astype(np.int64), od)
+    assert gs["near_ties"] == 0 and os_["near_ties"] == 0
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 12, 37, 100, 129, 200])
+def test_setup_matches_oracle(N):
+    A, B, p0 = instances.taixxa_like(N, 5 + N)
+    g = sa.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=1000)
+    o = oracle.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=1000)
+    _, cost, acc = g.result()
+    assert cost == o.state()["cost"] and acc == 0
+    assert np.array_equal(g.delta().astype(np.int64), packed_upper(o.delta()))
+    info = g.info()
+    T0, Tf, alpha = o.schedule()
+    assert (info["T0"], info["Tf"], info["alpha"]) == (T0, Tf, alpha)
+    for it in [0, 1, 255, 256, 999]:
+        assert g.temperature(it) == o.temperature(it)
+
+
+def test_config_n12_full_run():
+    """N = 12, uniform [0,99] symmetric, seed 1, random p0, T0 = 0.5 mean|Delta0|,
+    Tf = 1e-3 T0, I = 1e5."""
+    A, B, p0 = instances.taixxa_like(12, 1)
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=10 ** 5)
+    assert os_["accepts"] > 100
+    assert_same(gs, os_, gd, od)
+
+
+@pytest.mark.parametrize("N,I,seed", [(5, 20000, 2), (16, 100000, 3), (33, 200000, 4),
+                                      (64, 300000, 5), (100, 1000000, 1),
+                                      (129, 400000, 6), (200, 300000, 7)])
+def test_trajectory_matches_oracle(N, I, seed):
+    A, B, p0 = instances.taixxa_like(N, seed)
+    gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=I, seed=seed,
+                                     stream=seed)
+    assert os_["accepts"] > 0
+    assert_same(gs, os_, gd, od)
+
+
+def test_largest_tier1_size_partial_run():
+    N = sa.qap_sa_max_n()
+    assert N >= 200
+    A, B, p0 = instances.taixxa_like(N, 9)
+    gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=10 ** 7, seed=9,
+                                     oracle_iters=60000)
+    assert os_["accepts"] > 1000
+    assert_same(gs, os_, gd, od)
+
+
+def test_run_splitting_is_invisible():
+    A, B, p0 = instances.taixxa_like(50, 8)
+    I = 200000
+    splits = [1, 2, 3, 1000, 4093, 77777, I - 1 - 2 - 3 - 1000 - 4093 - 77777]
+    gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=I, seed=8,
+                                     splits=splits)
+    assert_same(gs, os_, gd, od)
+
+
+def test_hot_limit_every_proposal_accepted():
+    A, B, p0 = instances.taixxa_like(20, 3)
+    I = 3000
+    gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=1e300, tf=1e300, I=I,
+                                     relative=False)
+    assert gs["accepts"] == I
+    assert_same(gs, os_, gd, od)
+
+
+def test_cold_limit_descent():
+    A, B, p0 = instances.taixxa_like(40, 4)
+    I = 200000
+    gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=1e-300, tf=1e-300, I=I,
+                                     relative=False)
+    assert_same(gs, os_, gd, od)
+    assert gd.min() > 0  # a 2-swap local minimum
+
+
+def test_n2_and_n3_degenerate():
+    for N, seed in [(2, 1), (3, 2)]:
+        A, B, p0 = instances.taixxa_like(N, seed)
+        gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=5001)
+        assert_same(gs, os_, gd, od)
+    A = np.array([[0, 5], [5, 0]], dtype=np.int32)
+    B = np.array([[0, 3], [3, 0]], dtype=np.int32)
+    g = sa.Chain(A, B, np.array([1, 0], dtype=np.int32), t0=0.5, tf=1e-3,
+                 total_iters=1001)
+    g.run(1001)
+    p, cost, acc = g.result()
+    assert acc == 1001 and list(p) == [0, 1] and cost == 30
+
+
+def test_negative_entries_and_zero_matrix():
+    rng = np.random.default_rng(3)
+    N = 30
+    A = np.zeros((N, N), dtype=np.int32)
+    iu = np.triu_indices(N, 1)
+    A[iu] = rng.integers(-127, 128, size=len(iu[0]))
+    A = A + A.T
+    B = np.zeros((N, N), dtype=np.int32)
+    B[iu] = rng.integers(-127, 128, size=len(iu[0]))
+    B = B + B.T
+    p0 = rng.permutation(N).astype(np.int32)
+    gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=100000, seed=3)
+    assert_same(gs, os_, gd, od)
+    Z = np.zeros((N, N), dtype=np.int32)
+    gs, os_, gd, od, _, _ = run_both(Z, B, p0, t0=0.5, tf=1e-3, I=1000)
+    assert gs["accepts"] == 1000
+    assert_same(gs, os_, gd, od)
+
+
+def test_invalid_inputs_are_rejected():
+    A, B, p0 = instances.taixxa_like(10, 1)
+    kw = dict(t0=0.5, tf=1e-3, total_iters=100)
+    bad = A.copy()
+    bad[0, 1] += 1
+    with pytest.raises(sa.QapError) as e:
+        sa.Chain(bad, B, p0, **kw)
+    assert e.value.status == sa.QAP_E_INVAL
+    bad = B.copy()
+    bad[3, 3] = 1
+    with pytest.raises(sa.QapError) as e:
+        sa.Chain(A, bad, p0, **kw)
+    assert e.value.status == sa.QAP_E_INVAL
+    q = p0.copy()
+    q[0] = q[1]
+    with pytest.raises(sa.QapError) as e:
+        sa.Chain(A, B, q, **kw)
+    assert e.value.status == sa.QAP_E_INVAL
+    big = A.copy()
+    big[0, 1] = big[1, 0] = 128
+    with pytest.raises(sa.QapError) as e:
+        sa.Chain(big, B, p0, **kw)
+    assert e.value.status == sa.QAP_E_RANGE
+    with pytest.raises(sa.QapError) as e:
+        sa.Chain(A, B, p0, t0=0.5, tf=0.0, total_iters=100)
+    assert e.value.status == sa.QAP_E_INVAL
+    g = sa.Chain(A, B, p0, **kw)
+    g.run(60)
+    with pytest.raises(sa.QapError) as e:
+        g.run(41)
+    assert e.value.status == sa.QAP_E_RANGE
+    g.run(40)
+    n = sa.qap_sa_max_n()
+    A2, B2, p2 = instances.taixxa_like(n + 1, 1)
+    with pytest.raises(sa.QapError) as e:
+        sa.Chain(A2, B2, p2, **kw)
+    assert e.value.status == sa.QAP_E_UNSUPPORTED
+
+
+def test_device_pointer_entry_points_match_host_ones():
+    torch = pytest.importorskip("torch")
+    A, B, p0 = instances.taixxa_like(77, 12)
+    kw = dict(t0=0.5, tf=1e-3, total_iters=300000, seed=12)
+    h = sa.Chain(A, B, p0, **kw)
+    h.run(300000)
+    dev = torch.device("cuda:0")
+    At, Bt, pt = (torch.from_numpy(x).to(dev) for x in (A, B, p0))
+    s = torch.cuda.Stream()
+    d = sa.Chain.from_device(At, Bt, pt, stream=s.cuda_stream, **kw)
+    d.run(300000)
+    p_out = torch.zeros(77, dtype=torch.int32, device=dev)
+    c_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    a_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    sa.qap_sa_result_device(d.h, p_out.data_ptr(), c_out.data_ptr(), a_out.data_ptr())
+    s.synchronize()
+    hp, hc, ha = h.result()
+    assert np.array_equal(p_out.cpu().numpy(), hp)
+    assert int(c_out.item()) == hc and int(a_out.item()) == ha
+
+
+@pytest.mark.parametrize("N,I", [(100, 10 ** 8)])
+def test_full_size_single_chain_n100(N, I):
+    """The N = 100, I = 1e8 single-chain workload, whole run, against the oracle."""
+    A, B, p0 = instances.taixxa_like(N, 1)
+    gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=I, seed=1)
+    assert_same(gs, os_, gd, od)
