@@ -11,7 +11,9 @@
 #include <new>
 
 #include "qap_sa.h"
-#include "sa_kernels.cuh"
+#include "sa_tier1.cuh"
+
+#include <vector>
 
 using namespace qapsa;
 
@@ -51,12 +53,37 @@ int device_smem_optin() {
   return v;
 }
 
-// Row stride of the int8 A and B' rows: a whole number of 32-bit words, odd
-// so that threads reading different rows at the same word hit distinct banks.
+// Row stride of the int8 A and B' rows: 16 bytes times an odd number, so that
+// eight threads reading 16-byte chunks of eight consecutive rows hit distinct
+// bank groups.
 int row_stride(int N) {
-  int w = (N + 3) / 4;
-  if ((w & 1) == 0) ++w;
-  return 4 * w;
+  int c = (N + 15) / 16;
+  if ((c & 1) == 0) ++c;
+  return 16 * c;
+}
+
+// Height of the register tiles of Delta for a problem of size N.
+int tile_rows(int N) { return N <= 128 ? 4 : (N <= 192 ? 8 : 16); }
+
+int tile_bound(int R) {
+  return R == 4 ? T1Bound<4>::threads : (R == 8 ? T1Bound<8>::threads : T1Bound<16>::threads);
+}
+
+// R x 4 tiles of the upper triangle that hold at least one pair u < v < N,
+// row-block major, each encoded as first_row << 16 | first_column.
+std::vector<int> make_tiles(int N, int R) {
+  std::vector<int> t;
+  for (int u0 = 0; u0 < N - 1; u0 += R)
+    for (int v0 = 0; v0 < N; v0 += 4) {
+      bool any = false;
+      for (int i = 0; i < R && !any; ++i)
+        for (int c = 0; c < 4 && !any; ++c) {
+          const int u = u0 + i, v = v0 + c;
+          any = u < v && v < N;
+        }
+      if (any) t.push_back(u0 << 16 | v0);
+    }
+  return t;
 }
 
 int pow2_floor(int x) {
@@ -106,9 +133,11 @@ struct qap_sa {
   int *delta = nullptr, *p = nullptr, *d = nullptr;
   ChainStatus *st = nullptr;
   double *P = nullptr;
+  int *tiles = nullptr;
   Schedule sched;
   ChainDev dev{};
-  SmemLayout layout{};
+  T1Layout layout{};
+  int R = 4, nthreads = 0;
   unsigned long long it_host = 0;  // iterations enqueued so far
   int tier = 1;
 };
@@ -125,14 +154,26 @@ void free_handle(qap_sa *h) {
   cudaFree(h->d);
   cudaFree(h->st);
   cudaFree(h->P);
+  cudaFree(h->tiles);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
 
+// Threads of the tier-1 CTA: one per tile at least, and the whole register
+// budget of the kernel otherwise (more threads shorten the dependent chains of
+// the row recompute and the threshold preparation).
+int tier1_threads(int N, int ntiles) {
+  int nt = ntiles > N ? ntiles : N;
+  const int bound = tile_bound(tile_rows(N));
+  if (nt < bound) nt = bound;
+  return (nt + 31) & ~31;
+}
+
 int tier1_fits(int N) {
-  const int S = row_stride(N);
-  const int M = N * (N - 1) / 2;
-  return smem_layout(N, S, M).bytes <= device_smem_optin();
+  const int R = tile_rows(N);
+  const int nt = tier1_threads(N, (int)make_tiles(N, R).size());
+  if (nt > tile_bound(R)) return 0;
+  return t1_layout(N, row_stride(N)).bytes <= device_smem_optin();
 }
 
 int max_n_tier1() {
@@ -185,6 +226,10 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   CKF(cudaMalloc(&h->d, sizeof(int) * N));
   CKF(cudaMalloc(&h->st, sizeof(ChainStatus)));
   CKF(cudaMalloc(&h->P, sizeof(double) * 8 * 256));
+  const std::vector<int> tiles = make_tiles(N, tile_rows(N));
+  CKF(cudaMalloc(&h->tiles, sizeof(int) * (tiles.size() ? tiles.size() : 1)));
+  CKF(cudaMemcpyAsync(h->tiles, tiles.data(), sizeof(int) * tiles.size(),
+                      cudaMemcpyHostToDevice, stream));
   CKF(cudaMalloc(&count, sizeof(int) * N));
   CKF(cudaMalloc(&G, sizeof(int) * (size_t)N * N));
   CKF(cudaMalloc(&so, sizeof(SetupOut)));
@@ -245,8 +290,13 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   g.N = N;
   g.S = S;
   g.M = M;
-  g.tpv = N <= 32 ? 32 : pow2_floor(kThreads / N);
-  if (g.tpv > 32) g.tpv = 32;
+  h->R = tile_rows(N);
+  h->nthreads = tier1_threads(N, (int)tiles.size());
+  g.ntiles = (int)tiles.size();
+  g.tiles = h->tiles;
+  g.tpv = pow2_floor(h->nthreads / N);
+  if (g.tpv > 4) g.tpv = 4;  // >= 8 lanes per slice keep the 16-byte loads
+                             // of eight consecutive rows conflict-free
   g.A = h->A8;
   g.Bp = h->Bp8;
   g.delta = h->delta;
@@ -263,10 +313,16 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   // Pre-test margin: covers binary32 rounding of T and -ln u, the byte-table
   // product's drift from T0 alpha^it, and the exponent's rounding.
   g.mrel = (float)(2e-5 + 2e-7 * fabs(l2r) + 8.0 * (double)sc->total_iters * 0x1p-53);
-  h->layout = smem_layout(N, S, M);
-  CKF(cudaFuncSetAttribute(sa_cta_kernel,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           h->layout.bytes));
+  h->layout = t1_layout(N, S);
+  if (h->R == 4)
+    CKF(cudaFuncSetAttribute(sa_tier1_kernel<4>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, h->layout.bytes));
+  else if (h->R == 8)
+    CKF(cudaFuncSetAttribute(sa_tier1_kernel<8>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, h->layout.bytes));
+  else
+    CKF(cudaFuncSetAttribute(sa_tier1_kernel<16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, h->layout.bytes));
   CKF(cudaStreamSynchronize(stream));
   *out = h;
   return rc;
@@ -348,9 +404,14 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
   while (cur < end) {
     unsigned long long stop = cur + chunk_iters();
     if (stop > end) stop = end;
-    sa_cta_kernel<<<1, kThreads, h->layout.bytes, h->stream>>>(h->dev, stop);
+    if (h->R == 4)
+      sa_tier1_kernel<4><<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
+    else if (h->R == 8)
+      sa_tier1_kernel<8><<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
+    else
+      sa_tier1_kernel<16><<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "sa_cta_kernel launch");
+    if (e != cudaSuccess) return cuda_fail(e, "sa_tier1_kernel launch");
     cur = stop;
   }
   h->it_host = end;

@@ -1,0 +1,547 @@
+// sa_tier1.cuh -- tier 1 of the SA loop (Paul, arXiv:1208.2675, sections 2.2
+// and 3): one CTA runs the whole chain.
+//
+// Where the data lives during a run:
+//   Delta  registers: thread t owns an R x 4 tile of the upper triangle
+//          (rows u0..u0+R-1, columns v0..v0+3), so the O(1) update of a cell
+//          is three integer ops and the window scan reads registers;
+//   A, B'  shared memory, int8, rows of stride S = 16 x odd bytes (conflict-free
+//          128-bit loads in the rows-r,s recompute);
+//   a, b, d, p, the two recomputed rows, per-warp winner slots: shared memory.
+//
+// One accepted swap costs three block barriers:
+//   scan    every thread tests its tile's cells that fall in the window
+//           [it, it + K) of the cyclic proposal order against Eq. (2);
+//           redux.min per warp, atomicMin across warps      -> barrier
+//   stage   a_k = A_rk - A_sk, b_k = B'_sk - B'_rk (B' before the swap),
+//           d_k, the row/column swap of B' (Eq. 3), p        -> barrier
+//   update  O(1) update of every register cell; rows r,s from their
+//           definition through dp4a dot products into shared memory
+//                                                           -> barrier
+// and the recomputed rows are copied into the owning registers at the top of
+// the next scan (each thread reads only its own registers there).
+#pragma once
+#include "sa_common.cuh"
+
+namespace qapsa {
+
+struct T1Layout {
+  int off_A, off_B, off_a, off_b, off_d, off_p, off_nr, off_ns, off_slot, off_ctl;
+  int off_tt;
+  int bytes;
+};
+
+// Proposals of the next window whose Eq. (2) thresholds are prepared during
+// the update phase of an accepted swap.
+constexpr int kTabMax = 512;
+
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+// Vectors are padded so that tiles at the edge may read a few entries past N.
+__host__ __device__ inline int t1_vec_len(int N) { return ((N + 15) & ~15) + 16; }
+
+__host__ __device__ inline T1Layout t1_layout(int N, int S) {
+  T1Layout L;
+  const int NP = t1_vec_len(N);
+  int o = 0;
+  L.off_A = o;    o += align16(N * S);
+  L.off_B = o;    o += align16(N * S);
+  L.off_a = o;    o += 4 * NP;
+  L.off_b = o;    o += 4 * NP;
+  L.off_d = o;    o += 4 * NP;
+  L.off_p = o;    o += 4 * NP;
+  L.off_nr = o;   o += 4 * NP;
+  L.off_ns = o;   o += 4 * NP;
+  L.off_slot = o; o += 16 * 32;
+  L.off_ctl = o;  o += 128;
+  L.off_tt = o;   o += 8 * kTabMax;
+  L.bytes = o;
+  return L;
+}
+
+// Threads per CTA the kernel for tile height R is compiled for (register
+// budget: 65536 / bound per thread).
+template <int R> struct T1Bound;
+template <> struct T1Bound<4> { static constexpr int threads = 640; };
+template <> struct T1Bound<8> { static constexpr int threads = 640; };
+template <> struct T1Bound<16> { static constexpr int threads = 640; };
+
+// s_ctl words: three window keys, the d_r / d_s sums, the binary64 verdict,
+// then (from word 8, 8-byte aligned) thread 0's 64-bit counters.
+enum : int { kT1Key0 = 0, kT1Dr = 3, kT1Ds = 4, kT1Dec = 5 };
+enum : int { kC64Accepts = 0, kC64Cost = 1, kC64Near = 2, kC64Exact = 3, kC64Windows = 4 };
+
+__device__ __forceinline__ float u64_to_f32(unsigned long long x) {
+  return __uint2float_rn((unsigned)(x >> 32)) * 4294967296.0f +
+         __uint2float_rn((unsigned)x);
+}
+
+// Pair index of (u, v), u < v, in the row-major enumeration of pairs r < s.
+__device__ __forceinline__ int pidx(int N, int u, int v) {
+  return u * N - (u * (u + 1)) / 2 + (v - u - 1);
+}
+
+// Does the closed interval [lo, hi] of pair indices meet the window, which
+// starts at pair a and covers len <= M consecutive pairs, wrapping at M?
+__device__ __forceinline__ bool meets_window(int lo, int hi, int a, int len,
+                                             int M) {
+  const int end = a + len - 1;
+  if (end < M) return lo <= end && hi >= a;
+  return hi >= a || lo <= end - M;
+}
+
+// Binary32 pre-test interval for a proposal made at temperature ~Tc with
+// random word x: accept for sure if delta < lo, reject for sure if
+// delta > hi, otherwise decide in binary64.  t = Tc * (-ln u) and the margin
+// covers the binary32 errors of Tc, ln u and (float)delta (mrel relative,
+// 1e-6 Tc absolute).  A non-finite t gives NaN bounds: undecided.
+__device__ __forceinline__ float2 accept_interval(float mrel, float Tc,
+                                                  unsigned x) {
+  const float uf = fmaf(__uint2float_rn(x), 0x1p-32f, 0x1p-33f);
+  const float t = Tc * -logf(uf);
+  const float mg = mrel * t + 1e-6f * Tc;
+  return make_float2(t - mg, t + mg);
+}
+
+// Pre-test of up to four cells of one tile row that fall outside the prepared
+// table (long windows at low temperature, where survivors are rare).  Returns
+// the accepted cells in bits 0-3 and the undecided ones in bits 4-7.
+__device__ __noinline__ unsigned pretest_cells(unsigned long long seed,
+                                               unsigned stream, float log2a,
+                                               float mrel,
+                                               unsigned long long it, float Tw,
+                                               int j0, int j1, int j2, int j3,
+                                               int d0, int d1, int d2, int d3,
+                                               unsigned mask) {
+  const int jj[4] = {j0, j1, j2, j3};
+  const int dd[4] = {d0, d1, d2, d3};
+  unsigned long long qc = ~0ull;
+  uint4 xb = make_uint4(0, 0, 0, 0);
+  unsigned out = 0;
+  for (int c = 0; c < 4; ++c) {
+    if (!((mask >> c) & 1u)) continue;
+    const unsigned long long itc = it + (unsigned)jj[c];
+    if ((itc >> 2) != qc) {
+      qc = itc >> 2;
+      xb = rng_block(seed, stream, qc);
+    }
+    const float Tc = Tw * exp2f((float)jj[c] * log2a);
+    const float2 b = accept_interval(mrel, Tc, word_of(xb, (int)(itc & 3u)));
+    const float df = (float)dd[c];
+    if (df < b.x) out |= 1u << c;
+    else if (!(df > b.y)) out |= 16u << c;
+  }
+  return out;
+}
+
+template <int R>
+__global__ void __launch_bounds__(T1Bound<R>::threads, 1)
+    sa_tier1_kernel(ChainDev g, unsigned long long it_end) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = g.N, S = g.S, M = g.M;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthreads = blockDim.x;
+  const T1Layout L = t1_layout(N, S);
+  int8_t *s_A = reinterpret_cast<int8_t *>(smem + L.off_A);
+  int8_t *s_B = reinterpret_cast<int8_t *>(smem + L.off_B);
+  int *s_a = reinterpret_cast<int *>(smem + L.off_a);
+  int *s_b = reinterpret_cast<int *>(smem + L.off_b);
+  int *s_d = reinterpret_cast<int *>(smem + L.off_d);
+  int *s_p = reinterpret_cast<int *>(smem + L.off_p);
+  int *s_nr = reinterpret_cast<int *>(smem + L.off_nr);
+  int *s_ns = reinterpret_cast<int *>(smem + L.off_ns);
+  int4 *s_slot = reinterpret_cast<int4 *>(smem + L.off_slot);
+  unsigned *s_ctl = reinterpret_cast<unsigned *>(smem + L.off_ctl);
+  float2 *s_tt = reinterpret_cast<float2 *>(smem + L.off_tt);
+
+  // ---- chain state into shared memory and registers ----
+  {
+    const int4 *gA = reinterpret_cast<const int4 *>(g.A);
+    const int4 *gB = reinterpret_cast<const int4 *>(g.Bp);
+    int4 *sA = reinterpret_cast<int4 *>(s_A);
+    int4 *sB = reinterpret_cast<int4 *>(s_B);
+    for (int i = tid; i < (N * S) >> 4; i += nthreads) {
+      sA[i] = gA[i];
+      sB[i] = gB[i];
+    }
+  }
+  const int NP = t1_vec_len(N);
+  for (int i = tid; i < NP; i += nthreads) {
+    s_p[i] = i < N ? g.p[i] : 0;
+    s_d[i] = i < N ? g.d[i] : 0;
+    s_a[i] = 0;
+    s_b[i] = 0;
+  }
+  if (tid < 8) s_ctl[tid] = (tid < 3) ? kNone : 0u;
+
+  const bool has_tile = tid < g.ntiles;
+  int u0 = 0, v0 = 0;
+  if (has_tile) {
+    const int t = g.tiles[tid];
+    u0 = t >> 16;
+    v0 = t & 0xFFFF;
+  }
+  // Cell (u0+i, v0+c) is a pair iff u0+i < v0+c < N.
+  int D[R][4];
+  int tm_lo = 0x7FFFFFFF, tm_hi = -1;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int u = u0 + i, v = v0 + c;
+      D[i][c] = 0;
+      if (has_tile && u < v && v < N) {
+        const int m = pidx(N, u, v);
+        D[i][c] = g.delta[m];
+        tm_lo = min(tm_lo, m);
+        tm_hi = max(tm_hi, m);
+      }
+    }
+
+  unsigned long long *c64 = reinterpret_cast<unsigned long long *>(s_ctl + 8);
+  if (tid == 0) {
+    c64[kC64Accepts] = g.st->accepts;
+    c64[kC64Cost] = (unsigned long long)g.st->cost;
+    c64[kC64Near] = 0;
+    c64[kC64Exact] = 0;
+    c64[kC64Windows] = 0;
+  }
+  unsigned long long it = g.st->it;
+  int err = 0;
+  int mb = (int)(it % (unsigned long long)M);  // pair index of iteration it
+  int K = min(1024, M);                         // window length
+  unsigned wi = 0;
+  int pend_r = -1, pend_s = -1;
+  unsigned long long tab_it = 0;  // first iteration covered by s_tt
+  int tab_len = 0;                // entries of s_tt that are valid
+  const int tpv = g.tpv, lpt = 32 / tpv;  // lanes per dot-product slice
+  const int t_sl = lane / lpt, v_l = lane - t_sl * lpt;
+  const int vslots = (nthreads >> 5) * lpt;
+  const int NC = S >> 4;  // 16-byte chunks per row
+  __syncthreads();
+
+  for (;;) {
+    // ---- rows/columns r,s recomputed by the previous accept -> registers ----
+    if (pend_r >= 0 && has_tile) {
+      const int r = pend_r, s = pend_s;
+      if ((r >= u0 && r < u0 + R) || (s >= u0 && s < u0 + R)) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          const int u = u0 + i;
+          if (u == r || u == s) {
+            const int *src = (u == r) ? s_nr : s_ns;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) D[i][c] = src[v0 + c];
+          }
+        }
+      }
+      if ((r >= v0 && r < v0 + 4) || (s >= v0 && s < v0 + 4)) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int v = v0 + c;
+          if (v == r || v == s) {
+            const int *src = (v == r) ? s_nr : s_ns;
+#pragma unroll
+            for (int i = 0; i < R; ++i) D[i][c] = src[u0 + i];
+          }
+        }
+      }
+    }
+    pend_r = -1;
+    if (it >= it_end || err) break;
+
+    // ================= scan one window =================
+    // Window = iterations it .. it + wlen - 1, wlen <= M, so the proposal at
+    // offset j is pair (mb + j) mod M and every pair occurs at most once.
+    const int wlen = (int)min((unsigned long long)K, it_end - it);
+    // offset of this window in the prepared table (none if it lies outside)
+    const int jt0 = (it >= tab_it && it - tab_it < (unsigned long long)tab_len)
+                        ? (int)(it - tab_it) : kTabMax;
+    // Integer pre-filter for proposals beyond the table: -ln u <= 22.9 for
+    // u >= 2^-33, so delta > 24.5 T (T the window's largest binary32
+    // temperature) is rejected whatever u is.
+    float Tw = 0.0f;
+    int thr = 0;
+    if (jt0 + wlen > tab_len) {
+      Tw = g.T0f * exp2f(u64_to_f32(it) * g.log2a_f);
+      const float Te = Tw * exp2f((float)wlen * g.log2a_f);
+      const float tmax = fmaxf(Tw, Te) * 24.5f;
+      thr = (tmax < 1.0e9f) ? (int)ceilf(tmax) + 1 : 0x7FFFFFFF;
+    }
+    unsigned best = kNone;
+    int bu = 0, bv = 0, bd = 0;
+    if (has_tile && meets_window(tm_lo, tm_hi, mb, wlen, M)) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int u = u0 + i;
+        if (u >= N - 1 || u >= v0 + 3) continue;  // no pair u < v in this row
+        const int mrow = u * N - (u * (u + 1)) / 2 - u - 1;  // pidx(u,v) = mrow + v
+        const int vlo = max(v0, u + 1), vhi = min(v0 + 3, N - 1);
+        if (!meets_window(mrow + vlo, mrow + vhi, mb, wlen, M)) continue;
+        int jc[4];
+        unsigned acc = 0, unc = 0, slow = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          int j = mrow + v0 + c - mb;
+          if (j < 0) j += M;
+          jc[c] = j;
+          const int v = v0 + c;
+          if (v > u && v < N && j < wlen) {
+            const int dv = D[i][c];
+            const int jt = jt0 + j;
+            if (dv <= 0) {
+              acc |= 1u << c;
+            } else if (jt < tab_len) {
+              const float2 b = s_tt[jt];
+              const float df = (float)dv;
+              if (df < b.x) acc |= 1u << c;
+              else if (!(df > b.y)) unc |= 1u << c;
+            } else if (dv <= thr) {
+              slow |= 1u << c;
+            }
+          }
+        }
+        if (slow) {
+          const unsigned o = pretest_cells(g.seed, g.stream, g.log2a_f, g.mrel,
+                                           it, Tw, jc[0], jc[1], jc[2], jc[3],
+                                           D[i][0], D[i][1], D[i][2], D[i][3], slow);
+          acc |= o & 15u;
+          unc |= o >> 4;
+        }
+        const unsigned any = acc | unc;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if ((any >> c) & 1u) {
+            const unsigned key = ((unsigned)jc[c] << 1) | ((unc >> c) & 1u);
+            if (key < best) {
+              best = key;
+              bu = u;
+              bv = v0 + c;
+              bd = D[i][c];
+            }
+          }
+        }
+      }
+    }
+    const unsigned wmin = __reduce_min_sync(0xFFFFFFFFu, best);
+    if (wmin != kNone && best == wmin) {
+      s_slot[warp] = make_int4((int)best, bu, bv, bd);
+      atomicMin(s_ctl + kT1Key0 + (wi % 3u),
+                (((best >> 1) << 5 | (unsigned)warp) << 1) | (best & 1u));
+    }
+    __syncthreads();
+    const unsigned code = s_ctl[kT1Key0 + (wi % 3u)];
+    if (tid == 0) {
+      s_ctl[kT1Key0 + ((wi + 2u) % 3u)] = kNone;
+      ++c64[kC64Windows];
+    }
+    ++wi;
+
+    if (code == kNone) {  // nothing accepted in the window
+      mb += wlen;
+      if (mb >= M) mb -= M;
+      it += (unsigned)wlen;
+      K = min(K * 2, M);
+      continue;
+    }
+    const int j = (int)(code >> 6);
+    const int4 sl = s_slot[(code >> 1) & 31u];
+    const int r = sl.y, s = sl.z, dlt = sl.w;
+    if (code & 1u) {  // undecided by the binary32 pre-test: binary64
+      if (tid == 0) {
+        ++c64[kC64Exact];
+        s_ctl[kT1Dec] =
+            (unsigned)exact_accept(g.seed, g.stream, g.T0, g.P, dlt,
+                                   it + (unsigned)j, &c64[kC64Near]);
+      }
+      __syncthreads();
+      if (!s_ctl[kT1Dec]) {
+        it += (unsigned)j + 1;
+        mb += j + 1;
+        if (mb >= M) mb -= M;
+        continue;
+      }
+    }
+
+    // ================= accept the swap (r, s) =================
+    if (r < 0 || r >= s || s >= N) {
+      err = 1;
+      continue;
+    }
+    if (j < K / 8) K = max(64, K / 2);
+    K = min(K, M);
+    it += (unsigned)j + 1;
+    mb += j + 1;
+    if (mb >= M) mb -= M;
+    if (tid == 0) {
+      ++c64[kC64Accepts];
+      c64[kC64Cost] += (unsigned long long)(long long)dlt;
+    }
+
+    // ---- stage: a, b from B' before the swap; d; swap B' rows/cols; p ----
+    int dr_part = 0, ds_part = 0;
+    if (tid < N) {
+      const int k = tid;
+      const int Ark = s_A[r * S + k], Ask = s_A[s * S + k];
+      const int Brk = s_B[r * S + k], Bsk = s_B[s * S + k];
+      const int ak = Ark - Ask, bk = Bsk - Brk;
+      s_a[k] = 2 * ak;
+      s_b[k] = bk;
+      if (k != r && k != s) {
+        s_d[k] += ak * bk;
+        s_B[r * S + k] = (int8_t)Bsk;
+        s_B[s * S + k] = (int8_t)Brk;
+        s_B[k * S + r] = (int8_t)Bsk;
+        s_B[k * S + s] = (int8_t)Brk;
+        dr_part = Ark * Bsk;
+        ds_part = Ask * Brk;
+      } else if (k == s) {
+        dr_part = Ark * Brk;  // A_rs B'_rs
+      } else {
+        ds_part = Ask * Bsk;  // A_sr B'_sr
+      }
+      if (k == 0) {
+        const int t = s_p[r];
+        s_p[r] = s_p[s];
+        s_p[s] = t;
+      }
+    }
+    if (warp * 32 < N) {
+      dr_part = __reduce_add_sync(0xFFFFFFFFu, dr_part);
+      ds_part = __reduce_add_sync(0xFFFFFFFFu, ds_part);
+      if (lane == 0) {
+        atomicAdd(reinterpret_cast<int *>(s_ctl + kT1Dr), dr_part);
+        atomicAdd(reinterpret_cast<int *>(s_ctl + kT1Ds), ds_part);
+      }
+    }
+    __syncthreads();
+    const int dr = (int)s_ctl[kT1Dr], ds = (int)s_ctl[kT1Ds];
+
+    // ---- thresholds of the next window [it, it + tab_len), one Philox
+    //      block per thread ----
+    tab_it = it;
+    tab_len = min(K, kTabMax);
+    {
+      const int o = (int)(it & 3u);
+      const int nblk = (tab_len + o + 3) >> 2;
+      const int qb = nthreads - 1 - tid;  // the last warps do this: they have
+                                          // the least of the other work
+      if (qb < nblk) {
+        const unsigned long long q = (it >> 2) + (unsigned)qb;
+        const uint4 x = rng_block(g.seed, g.stream, q);
+        const float Tq = g.T0f * exp2f(u64_to_f32(q << 2) * g.log2a_f);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int jt = 4 * qb + w - o;
+          if (jt >= 0 && jt < tab_len)
+            s_tt[jt] = accept_interval(g.mrel, Tq * exp2f((float)w * g.log2a_f),
+                                       word_of(x, w));
+        }
+      }
+    }
+
+    // ---- rows r,s under the new p through G_xy = <A_x, B'_y>:
+    //      Delta_rv = 2 (G_rv + G_vr - d_r - d_v + 2 A_rv B'_rv) ----
+    {
+      const int4 *Ar4 = reinterpret_cast<const int4 *>(s_A + r * S);
+      const int4 *As4 = reinterpret_cast<const int4 *>(s_A + s * S);
+      const int4 *Br4 = reinterpret_cast<const int4 *>(s_B + r * S);
+      const int4 *Bs4 = reinterpret_cast<const int4 *>(s_B + s * S);
+      for (int vb = 0; vb < N; vb += vslots) {
+        const int v = vb + warp * lpt + v_l;
+        int g1 = 0, g2 = 0, g3 = 0, g4 = 0;
+        if (v < N) {
+          const int4 *Av4 = reinterpret_cast<const int4 *>(s_A + v * S);
+          const int4 *Bv4 = reinterpret_cast<const int4 *>(s_B + v * S);
+#pragma unroll 1
+          for (int c = t_sl; c < NC; c += tpv) {
+            const int4 bv = Bv4[c];
+            int4 x = Ar4[c];
+            g1 = __dp4a(x.x, bv.x, g1); g1 = __dp4a(x.y, bv.y, g1);
+            g1 = __dp4a(x.z, bv.z, g1); g1 = __dp4a(x.w, bv.w, g1);
+            x = As4[c];
+            g2 = __dp4a(x.x, bv.x, g2); g2 = __dp4a(x.y, bv.y, g2);
+            g2 = __dp4a(x.z, bv.z, g2); g2 = __dp4a(x.w, bv.w, g2);
+            const int4 av = Av4[c];
+            x = Br4[c];
+            g3 = __dp4a(av.x, x.x, g3); g3 = __dp4a(av.y, x.y, g3);
+            g3 = __dp4a(av.z, x.z, g3); g3 = __dp4a(av.w, x.w, g3);
+            x = Bs4[c];
+            g4 = __dp4a(av.x, x.x, g4); g4 = __dp4a(av.y, x.y, g4);
+            g4 = __dp4a(av.z, x.z, g4); g4 = __dp4a(av.w, x.w, g4);
+          }
+        }
+        for (int o = lpt; o < 32; o <<= 1) {
+          g1 += __shfl_xor_sync(0xFFFFFFFFu, g1, o);
+          g2 += __shfl_xor_sync(0xFFFFFFFFu, g2, o);
+          g3 += __shfl_xor_sync(0xFFFFFFFFu, g3, o);
+          g4 += __shfl_xor_sync(0xFFFFFFFFu, g4, o);
+        }
+        if (t_sl == 0 && v < N && v != r && v != s) {
+          const int dv = s_d[v];
+          const int Arv = s_A[r * S + v], Brv = s_B[r * S + v];
+          const int Asv = s_A[s * S + v], Bsv = s_B[s * S + v];
+          s_nr[v] = 2 * (g1 + g3 - dr - dv + 2 * Arv * Brv);
+          s_ns[v] = 2 * (g2 + g4 - ds - dv + 2 * Asv * Bsv);
+        }
+      }
+    }
+    // ---- O(1) update of every register cell: Delta_uv += 2 (a_u - a_v)(b_v - b_u);
+    //      cells in rows/columns r,s are overwritten from s_nr/s_ns later ----
+    if (has_tile) {
+      const int4 av = *reinterpret_cast<const int4 *>(s_a + v0);
+      const int4 bv = *reinterpret_cast<const int4 *>(s_b + v0);
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int au = s_a[u0 + i], bu_ = s_b[u0 + i];
+        D[i][0] += (au - av.x) * (bv.x - bu_);
+        D[i][1] += (au - av.y) * (bv.y - bu_);
+        D[i][2] += (au - av.z) * (bv.z - bu_);
+        D[i][3] += (au - av.w) * (bv.w - bu_);
+      }
+    }
+    if (tid == 0) {
+      s_nr[s] = -dlt;
+      s_ns[r] = -dlt;
+      s_d[r] = dr;
+      s_d[s] = ds;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_ctl[kT1Dr] = 0u;
+      s_ctl[kT1Ds] = 0u;
+    }
+    pend_r = r;
+    pend_s = s;
+  }
+
+  // ---- state back to global memory ----
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int u = u0 + i, v = v0 + c;
+      if (has_tile && u < v && v < N) g.delta[pidx(N, u, v)] = D[i][c];
+    }
+  __syncthreads();
+  {
+    const int4 *sB = reinterpret_cast<const int4 *>(s_B);
+    int4 *gB = reinterpret_cast<int4 *>(g.Bp);
+    for (int i = tid; i < (N * S) >> 4; i += nthreads) gB[i] = sB[i];
+  }
+  for (int i = tid; i < N; i += nthreads) {
+    g.p[i] = s_p[i];
+    g.d[i] = s_d[i];
+  }
+  if (tid == 0) {
+    g.st->it = it;
+    g.st->accepts = c64[kC64Accepts];
+    g.st->cost = (long long)c64[kC64Cost];
+    g.st->near_ties += c64[kC64Near];
+    g.st->exact_evals += c64[kC64Exact];
+    g.st->windows += c64[kC64Windows];
+    if (err) g.st->error = err;
+  }
+}
+
+}  // namespace qapsa

@@ -81,7 +81,7 @@ def test_config_n12_full_run():
 
 @pytest.mark.parametrize("N,I,seed", [(5, 20000, 2), (16, 100000, 3), (33, 200000, 4),
                                       (64, 300000, 5), (100, 1000000, 1),
-                                      (129, 400000, 6), (200, 300000, 7)])
+                                      (129, 400000, 6), (160, 300000, 10), (200, 300000, 7)])
 def test_trajectory_matches_oracle(N, I, seed):
     A, B, p0 = instances.taixxa_like(N, seed)
     gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=I, seed=seed,
@@ -225,4 +225,14 @@ def test_full_size_single_chain_n100(N, I):
     """The N = 100, I = 1e8 single-chain workload, whole run, against the oracle."""
     A, B, p0 = instances.taixxa_like(N, 1)
     gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=I, seed=1)
+    assert_same(gs, os_, gd, od)
+
+
+def test_n256_workload_prefix_matches_oracle():
+    """N = 256 under the I = 1e9 schedule: the first 1e5 iterations (the
+    high-acceptance start, about 2e4 accepted swaps) against the oracle."""
+    A, B, p0 = instances.taixxa_like(256, 1)
+    gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=10 ** 9, seed=1,
+                                     oracle_iters=100000)
+    assert os_["accepts"] > 10000
     assert_same(gs, os_, gd, od)
