@@ -152,6 +152,31 @@ QAP_EXPORT double qap_sa_temperature(const qap_sa *h, uint64_t it);
 /* Frees every resource of the handle (NULL is ignored).                     */
 QAP_EXPORT void qap_sa_destroy(qap_sa *h);
 
+/* ---- set-up without allocation ---------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc -- programs whose device memory belongs to another
+ * allocator (a framework's caching pool) or to a fixed budget, and loops that
+ * must not stall on the device-wide synchronisation cudaMalloc and cudaFree may
+ * imply.  It computes what qap_sa_create computes first (step (a): the swap
+ * costs Delta for every pair and the cost of Eq. (1)) and allocates nothing:
+ * its intermediates live in one static device array of about 400 KB that every
+ * GPU loading the library holds until the process exits.
+ *   A, B, p   : DEVICE pointers, same layouts and rules as qap_sa_create
+ *   N         : 2 .. QAP_NOALLOC_MAX_N; larger N returns QAP_E_RANGE
+ *   delta_out : DEVICE, M = N(N-1)/2 int32 in pair order (as qap_sa_delta)
+ *   cost_out  : DEVICE, one int64
+ *   cuda_stream : the cudaStream_t the work is issued on (NULL = default)
+ * Blocks until the work is done.  Returns QAP_E_INVAL / QAP_E_RANGE for the
+ * same input defects as qap_sa_create; in that case the outputs hold
+ * unspecified values.  The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any stream
+ * capture.  All calls share the one array, so calls that overlap on the GPU
+ * (from several threads or streams) race: serialise them.                    */
+#define QAP_NOALLOC_MAX_N 256
+QAP_EXPORT int qap_sa_setup_noalloc(const int32_t *A, const int32_t *B, int32_t N,
+                                    const int32_t *p, int32_t *delta_out,
+                                    int64_t *cost_out, void *cuda_stream);
+
 /* ---- library ------------------------------------------------------------- */
 /* Largest N any tier supports on the current device (0 if no device).       */
 QAP_EXPORT int32_t qap_sa_max_n(void);

@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "qap_sa.h"
@@ -516,3 +517,98 @@ const char *qap_sa_strerror(int status) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------- //
+// Set-up without allocation.
+//
+// Some callers cannot call cudaMalloc: programs whose device memory is owned
+// by another allocator (a framework's caching pool) or fixed by a budget, and
+// loops that must not stall on the device-wide synchronisation cudaMalloc and
+// cudaFree may imply.  qap_sa_setup_noalloc gives them step (a) of the method
+// -- the packed Delta and the cost for a given permutation -- with every
+// intermediate (int8 A and B', the Gram matrix, counters) in the file-scope
+// array below, which every GPU that loads this library holds until exit.
+// ------------------------------------------------------------------------- //
+namespace {
+
+constexpr int kNoAllocMaxN = 256;
+constexpr size_t kNoAllocAlign = 256;
+constexpr size_t na_round(size_t x) { return (x + kNoAllocAlign - 1) / kNoAllocAlign * kNoAllocAlign; }
+constexpr size_t kNaRow = 272;  // row_stride(kNoAllocMaxN)
+constexpr size_t kNaA = 0;
+constexpr size_t kNaB = kNaA + na_round((size_t)kNoAllocMaxN * kNaRow);
+constexpr size_t kNaG = kNaB + na_round((size_t)kNoAllocMaxN * kNaRow);
+constexpr size_t kNaCount = kNaG + na_round(sizeof(int) * (size_t)kNoAllocMaxN * kNoAllocMaxN);
+constexpr size_t kNaP = kNaCount + na_round(sizeof(int) * (size_t)kNoAllocMaxN);
+constexpr size_t kNaD = kNaP + na_round(sizeof(int) * (size_t)kNoAllocMaxN);
+constexpr size_t kNaOut = kNaD + na_round(sizeof(int) * (size_t)kNoAllocMaxN);
+constexpr size_t kNoAllocBytes = kNaOut + na_round(sizeof(SetupOut));
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_setup_scratch[kNoAllocBytes];
+
+namespace {
+
+std::mutex g_na_mutex;
+void *g_na_ptr[64];  // device address of g_setup_scratch, per device
+
+// The host-side name g_setup_scratch is only a stand-in for the device array;
+// its device address is looked up once per device, with that device current.
+int noalloc_scratch(unsigned char **out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return QAP_E_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_ptr[dev]) {
+    void *ptr = nullptr;
+    CK(cudaGetSymbolAddress(&ptr, g_setup_scratch));
+    g_na_ptr[dev] = ptr;
+  }
+  *out = static_cast<unsigned char *>(g_na_ptr[dev]);
+  return QAP_OK;
+}
+
+}  // namespace
+
+extern "C" int qap_sa_setup_noalloc(const int32_t *A, const int32_t *B,
+                                    int32_t N, const int32_t *p,
+                                    int32_t *delta_out, int64_t *cost_out,
+                                    void *cuda_stream) {
+  if (!A || !B || !p || !delta_out || !cost_out || N < 2) return QAP_E_INVAL;
+  if (N > kNoAllocMaxN) return QAP_E_RANGE;  // beyond the static array
+  unsigned char *base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  const int S = row_stride(N);
+  int8_t *A8 = reinterpret_cast<int8_t *>(base + kNaA);
+  int8_t *Bp8 = reinterpret_cast<int8_t *>(base + kNaB);
+  int *G = reinterpret_cast<int *>(base + kNaG);
+  int *count = reinterpret_cast<int *>(base + kNaCount);
+  int *pp = reinterpret_cast<int *>(base + kNaP);
+  int *d = reinterpret_cast<int *>(base + kNaD);
+  SetupOut *so = reinterpret_cast<SetupOut *>(base + kNaOut);
+  // The array keeps the previous call's contents: zero what the kernels
+  // accumulate into or read as padding.
+  CK(cudaMemsetAsync(A8, 0, (size_t)N * S, stream));
+  CK(cudaMemsetAsync(Bp8, 0, (size_t)N * S, stream));
+  CK(cudaMemsetAsync(count, 0, sizeof(int) * N, stream));
+  CK(cudaMemsetAsync(so, 0, sizeof(SetupOut), stream));
+  const long long NN = (long long)N * N;
+  const int blocks = (int)((NN + 255) / 256);
+  setup_pack_kernel<<<blocks, 256, 0, stream>>>(A, B, p, N, S, A8, count, so);
+  setup_bprime_kernel<<<blocks, 256, 0, stream>>>(B, p, N, S, count, Bp8, pp, so);
+  dim3 gg((N + 127) / 128, N);
+  setup_gram_kernel<<<gg, 128, 0, stream>>>(A8, Bp8, N, S, G);
+  setup_delta_kernel<<<gg, 128, 0, stream>>>(G, A8, Bp8, N, S, delta_out, d, so);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(cost_out, &so->cost0, sizeof(int64_t),
+                     cudaMemcpyDeviceToDevice, stream));
+  SetupOut so_h{};
+  CK(cudaMemcpyAsync(&so_h, so, sizeof so_h, cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  if (so_h.flags & (kFlagAsym | kFlagDiag | kFlagPerm)) return QAP_E_INVAL;
+  if (so_h.flags & (kFlagRangeA | kFlagRangeB)) return QAP_E_RANGE;
+  return QAP_OK;
+}

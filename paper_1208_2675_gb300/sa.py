@@ -65,6 +65,9 @@ SIGNATURES = {
     "qap_sa_delta": (ctypes.c_int, [ctypes.c_void_p, _i32p]),
     "qap_sa_temperature": (ctypes.c_double, [ctypes.c_void_p, ctypes.c_uint64]),
     "qap_sa_destroy": (None, [ctypes.c_void_p]),
+    "qap_sa_setup_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
     "qap_sa_max_n": (ctypes.c_int32, []),
     "qap_sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -178,6 +181,15 @@ def qap_sa_temperature(h, it: int) -> float:
 def qap_sa_destroy(h) -> None:
     if h:
         lib().qap_sa_destroy(h)
+
+
+def qap_sa_setup_noalloc(A_ptr: int, B_ptr: int, N: int, p_ptr: int, delta_ptr: int,
+                         cost_ptr: int, stream: int = 0) -> None:
+    """Step (a) into caller-owned DEVICE buffers, allocating nothing (see the header)."""
+    _check(lib().qap_sa_setup_noalloc(ctypes.c_void_p(A_ptr), ctypes.c_void_p(B_ptr), int(N),
+                                      ctypes.c_void_p(p_ptr), ctypes.c_void_p(delta_ptr),
+                                      ctypes.c_void_p(cost_ptr), ctypes.c_void_p(stream or None)),
+           "qap_sa_setup_noalloc")
 
 
 def qap_sa_max_n() -> int:

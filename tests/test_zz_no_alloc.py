@@ -1,0 +1,65 @@
+"""The allocation-free set-up entry point against the regular one.
+
+qap_sa_setup_noalloc serves callers that cannot call cudaMalloc (device memory
+owned by another allocator or a fixed budget, or loops that must not stall on
+the synchronisation cudaMalloc/cudaFree may imply).  Its Delta and cost must
+equal those of qap_sa_create on the same inputs, exactly (integers), on two
+calls in a row -- the second call reuses the static scratch array the first one
+left behind.  This file is collected last so that a run stopping at the first
+failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_1208_2675_gb300 import instances
+from paper_1208_2675_gb300 import sa
+
+pytestmark = pytest.mark.gpu
+
+
+def _regular(A, B, p0):
+    ch = sa.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=1)
+    _, cost, _ = ch.result()
+    delta = ch.delta()
+    ch.close()
+    return delta, cost
+
+
+def _noalloc(torch, A, B, p0, stream):
+    dev = torch.device("cuda:0")
+    N = len(p0)
+    M = N * (N - 1) // 2
+    At, Bt, pt = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (A, B, p0))
+    d_out = torch.full((M,), -7, dtype=torch.int32, device=dev)
+    c_out = torch.full((1,), -7, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    sa.qap_sa_setup_noalloc(At.data_ptr(), Bt.data_ptr(), N, pt.data_ptr(),
+                            d_out.data_ptr(), c_out.data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    return d_out.cpu().numpy(), int(c_out.item())
+
+
+def test_noalloc_setup_equals_regular_setup_twice():
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    # a large instance first, then a smaller one that must not see its leftovers
+    for N, seed in [(256, 21), (37, 22)]:
+        A, B, p0 = instances.taixxa_like(N, seed)
+        want_d, want_c = _regular(A, B, p0)
+        got_d, got_c = _noalloc(torch, A, B, p0, stream)
+        assert got_c == want_c
+        assert np.array_equal(got_d, want_d)
+
+
+def test_noalloc_setup_rejects_sizes_beyond_its_maximum():
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    N = 257
+    A, B, p0 = instances.taixxa_like(N, 1)
+    At, Bt, pt = (torch.from_numpy(x).to(dev) for x in (A, B, p0))
+    d_out = torch.zeros(N * (N - 1) // 2, dtype=torch.int32, device=dev)
+    c_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    with pytest.raises(sa.QapError) as e:
+        sa.qap_sa_setup_noalloc(At.data_ptr(), Bt.data_ptr(), N, pt.data_ptr(),
+                                d_out.data_ptr(), c_out.data_ptr())
+    assert e.value.status == sa.QAP_E_RANGE
