@@ -152,6 +152,39 @@ QAP_EXPORT double qap_sa_temperature(const qap_sa *h, uint64_t it);
 /* Frees every resource of the handle (NULL is ignored).                     */
 QAP_EXPORT void qap_sa_destroy(qap_sa *h);
 
+/* ---- batch of independent chains ------------------------------------------
+ * Many independent chains -- the "independent runs" of section 2.3, here
+ * independent problems of uneven N -- advanced together by one persistent
+ * launch captured in a CUDA graph: each CTA of a one-CTA-per-SM grid takes
+ * the next chain from a longest-first work list and runs it with the same
+ * kernel code as a single chain, so every chain's trajectory equals the one
+ * qap_sa_run gives it alone.                                                */
+typedef struct qap_problem {
+  const int32_t *A;     /* host, N*N int32, as for qap_sa_create            */
+  const int32_t *B;     /* host, N*N int32                                  */
+  const int32_t *p0;    /* host, N int32 permutation                        */
+  int32_t N;
+  uint32_t reserved;    /* must be 0                                        */
+  qap_schedule sched;   /* its own schedule and random stream (stream_id)   */
+  uint64_t seed;
+} qap_problem;
+
+typedef struct qap_batch qap_batch; /* opaque; freed by qap_batch_destroy */
+
+/* Set-up (step (a)) of every problem; host inputs are read during the call
+ * only.  Errors as qap_sa_create, for the first problem that fails.         */
+QAP_EXPORT int qap_batch_create(const qap_problem *probs, int32_t count,
+                                qap_batch **out);
+/* Advances chain i by iters[i] iterations (iters == NULL: every chain to its
+ * total_iters) in one graph launch; blocks until done.  QAP_E_RANGE if a
+ * chain would pass its total_iters (nothing runs then).                     */
+QAP_EXPORT int qap_batch_run(qap_batch *b, const uint64_t *iters);
+/* State of chain i, as qap_sa_result / qap_sa_get_info.                      */
+QAP_EXPORT int qap_batch_result(qap_batch *b, int32_t i, int32_t *p_out,
+                                int64_t *cost, uint64_t *accepts);
+QAP_EXPORT int qap_batch_get_info(qap_batch *b, int32_t i, qap_sa_info *out);
+QAP_EXPORT void qap_batch_destroy(qap_batch *b);
+
 /* ---- set-up without allocation ---------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot call cudaMalloc -- programs whose device memory belongs to another

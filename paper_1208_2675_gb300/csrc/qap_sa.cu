@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 
@@ -350,13 +351,17 @@ int validate_args(const void *A, const void *B, int32_t N, const void *p0,
 
 extern "C" {
 
-int qap_sa_create(const int32_t *A, const int32_t *B, int32_t N,
-                  const int32_t *p0, const qap_schedule *sched, uint64_t seed,
-                  qap_sa **out) {
-  int rc = validate_args(A, B, N, p0, sched, out);
-  if (rc) return rc;
-  cudaStream_t st = nullptr;
-  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+}  // extern "C"
+
+namespace {
+
+// Copies host A, B, p0 to temporary device buffers and runs create_common on
+// `st` (owned by the handle if own_stream).
+int create_from_host(const int32_t *A, const int32_t *B, int32_t N,
+                     const int32_t *p0, const qap_schedule *sched,
+                     uint64_t seed, cudaStream_t st, bool own_stream,
+                     qap_sa **out) {
+  int rc = QAP_OK;
   int32_t *dA = nullptr, *dB = nullptr, *dp = nullptr;
   const size_t nn = sizeof(int32_t) * (size_t)N * N;
   cudaError_t e = cudaMalloc(&dA, nn);
@@ -368,19 +373,34 @@ int qap_sa_create(const int32_t *A, const int32_t *B, int32_t N,
     e = cudaMemcpyAsync(dp, p0, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) {
     rc = cuda_fail(e, "staging copy");
+    cudaStreamSynchronize(st);
     cudaFree(dA);
     cudaFree(dB);
     cudaFree(dp);
-    cudaStreamDestroy(st);
+    if (own_stream) cudaStreamDestroy(st);
     return rc;
   }
   // create_common synchronises the stream before it returns, and on failure
-  // destroys it together with the partial handle.
-  rc = create_common(dA, dB, N, dp, sched, seed, st, true, out);
+  // destroys an owned stream together with the partial handle.
+  rc = create_common(dA, dB, N, dp, sched, seed, st, own_stream, out);
   cudaFree(dA);
   cudaFree(dB);
   cudaFree(dp);
-  return rc;  // on failure create_common destroyed the stream with the handle
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qap_sa_create(const int32_t *A, const int32_t *B, int32_t N,
+                  const int32_t *p0, const qap_schedule *sched, uint64_t seed,
+                  qap_sa **out) {
+  int rc = validate_args(A, B, N, p0, sched, out);
+  if (rc) return rc;
+  cudaStream_t st = nullptr;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  return create_from_host(A, B, N, p0, sched, seed, st, true, out);
 }
 
 int qap_sa_create_device(const int32_t *A, const int32_t *B, int32_t N,
@@ -515,6 +535,163 @@ const char *qap_sa_strerror(int status) {
     default: return "unknown status";
   }
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------- //
+// Batch of independent chains.
+// ------------------------------------------------------------------------- //
+struct qap_batch {
+  int count = 0;
+  std::vector<qap_sa *> h;
+  std::vector<BatchChain> chains;
+  cudaStream_t stream = nullptr;
+  BatchChain *d_chains = nullptr;
+  int *d_order = nullptr;
+  int *d_counter = nullptr;
+  int smem = 0;
+  int grid = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void free_batch(qap_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (qap_sa *h : b->h) free_handle(h);
+  cudaFree(b->d_chains);
+  cudaFree(b->d_order);
+  cudaFree(b->d_counter);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qap_batch_create(const qap_problem *probs, int32_t count, qap_batch **out) {
+  if (!out) return QAP_E_INVAL;
+  *out = nullptr;
+  if (!probs || count < 1) return QAP_E_INVAL;
+  qap_batch *b = new (std::nothrow) qap_batch();
+  if (!b) return QAP_E_NOMEM;
+  b->count = count;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  for (int i = 0; i < count; ++i) {
+    const qap_problem &q = probs[i];
+    qap_sa *h = nullptr;
+    int rc = validate_args(q.A, q.B, q.N, q.p0, &q.sched, &h);
+    if (!rc) rc = create_from_host(q.A, q.B, q.N, q.p0, &q.sched, q.seed, b->stream,
+                                   false, &h);
+    if (rc) {
+      free_batch(b);
+      return rc;
+    }
+    b->h.push_back(h);
+    BatchChain bc{};
+    bc.g = h->dev;
+    bc.it_end = 0;
+    bc.R = h->R;
+    b->chains.push_back(bc);
+    if (h->layout.bytes > b->smem) b->smem = h->layout.bytes;
+  }
+  // work list: most work first (N^2 I)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    const double wx = (double)b->h[x]->N * b->h[x]->N * (double)b->h[x]->sched.I;
+    const double wy = (double)b->h[y]->N * b->h[y]->N * (double)b->h[y]->sched.I;
+    return wx > wy;
+  });
+  int dev = 0, sms = 0;
+  auto fail = [&](cudaError_t err, const char *what) {
+    int rc = cuda_fail(err, what);
+    free_batch(b);
+    return rc;
+  };
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return fail(e, "cudaGetDevice");
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return fail(e, "cudaDeviceGetAttribute");
+  b->grid = count < sms ? count : sms;
+  if ((e = cudaMalloc(&b->d_chains, sizeof(BatchChain) * count)) != cudaSuccess)
+    return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&b->d_order, sizeof(int) * count)) != cudaSuccess)
+    return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&b->d_counter, sizeof(int))) != cudaSuccess)
+    return fail(e, "cudaMalloc");
+  if ((e = cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * count,
+                           cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
+    return fail(e, "cudaMemcpyAsync");
+  if ((e = cudaFuncSetAttribute(sa_batch_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                b->smem)) != cudaSuccess)
+    return fail(e, "cudaFuncSetAttribute");
+  // The whole run is one graph: reset the work counter, one persistent launch.
+  cudaGraph_t graph = nullptr;
+  if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return fail(e, "cudaStreamBeginCapture");
+  cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
+  sa_batch_kernel<<<b->grid, kBatchThreads, b->smem, b->stream>>>(
+      b->d_chains, b->d_order, count, b->d_counter);
+  if ((e = cudaStreamEndCapture(b->stream, &graph)) != cudaSuccess)
+    return fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(e, "cudaGraphInstantiate");
+  if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+    return fail(e, "cudaStreamSynchronize");
+  *out = b;
+  return QAP_OK;
+}
+
+int qap_batch_run(qap_batch *b, const uint64_t *iters) {
+  if (!b) return QAP_E_INVAL;
+  for (int i = 0; i < b->count; ++i) {
+    qap_sa *h = b->h[i];
+    const uint64_t want = iters ? iters[i] : h->sched.I - h->it_host;
+    if (want > h->sched.I - h->it_host) return QAP_E_RANGE;
+  }
+  for (int i = 0; i < b->count; ++i) {
+    qap_sa *h = b->h[i];
+    const uint64_t want = iters ? iters[i] : h->sched.I - h->it_host;
+    b->chains[i].it_end = h->it_host + want;
+  }
+  CK(cudaMemcpyAsync(b->d_chains, b->chains.data(), sizeof(BatchChain) * b->count,
+                     cudaMemcpyHostToDevice, b->stream));
+  CK(cudaGraphLaunch(b->exec, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  std::vector<ChainStatus> st(b->count);
+  for (int i = 0; i < b->count; ++i)
+    CK(cudaMemcpyAsync(&st[i], b->h[i]->st, sizeof(ChainStatus),
+                       cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  int rc = QAP_OK;
+  for (int i = 0; i < b->count; ++i) {
+    b->h[i]->it_host = b->chains[i].it_end;
+    if (st[i].error || st[i].it != b->chains[i].it_end) rc = QAP_E_STATE;
+  }
+  return rc;
+}
+
+int qap_batch_result(qap_batch *b, int32_t i, int32_t *p_out, int64_t *cost,
+                     uint64_t *accepts) {
+  if (!b || i < 0 || i >= b->count) return QAP_E_INVAL;
+  return qap_sa_result(b->h[i], p_out, cost, accepts);
+}
+
+int qap_batch_get_info(qap_batch *b, int32_t i, qap_sa_info *out) {
+  if (!b || i < 0 || i >= b->count) return QAP_E_INVAL;
+  return qap_sa_get_info(b->h[i], out);
+}
+
+void qap_batch_destroy(qap_batch *b) { free_batch(b); }
 
 }  // extern "C"
 

@@ -134,10 +134,12 @@ __device__ __noinline__ unsigned pretest_cells(unsigned long long seed,
   return out;
 }
 
+// One chain, run by the whole CTA from its state in global memory to iteration
+// it_end and written back.  `smem` holds at least t1_layout(N, S).bytes.
 template <int R>
-__global__ void __launch_bounds__(T1Bound<R>::threads, 1)
-    sa_tier1_kernel(ChainDev g, unsigned long long it_end) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void t1_run_chain(const ChainDev &g,
+                                             unsigned long long it_end,
+                                             unsigned char *smem) {
   const int N = g.N, S = g.S, M = g.M;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthreads = blockDim.x;
@@ -541,6 +543,47 @@ __global__ void __launch_bounds__(T1Bound<R>::threads, 1)
     g.st->exact_evals += c64[kC64Exact];
     g.st->windows += c64[kC64Windows];
     if (err) g.st->error = err;
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(T1Bound<R>::threads, 1)
+    sa_tier1_kernel(ChainDev g, unsigned long long it_end) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  t1_run_chain<R>(g, it_end, smem);
+}
+
+// ------------------------------------------------------------------------- //
+// Batch of independent chains (no counterpart in the paper's single-chain
+// method; the paper motivates it only as "independent runs").  A persistent
+// grid: every CTA takes the next chain from a work list (longest first) with
+// one atomic, runs it to its iteration target with the tier-1 code, and takes
+// the next, until the list is empty.
+// ------------------------------------------------------------------------- //
+struct BatchChain {
+  ChainDev g;
+  unsigned long long it_end;
+  int R;
+  int pad;
+};
+
+constexpr int kBatchThreads = 640;
+
+__global__ void __launch_bounds__(kBatchThreads, 1)
+    sa_batch_kernel(const BatchChain *__restrict__ chains,
+                    const int *__restrict__ order, int n, int *counter) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_next;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int k = s_next;
+    if (k >= n) return;
+    const BatchChain &bc = chains[order[k]];
+    if (bc.R == 4) t1_run_chain<4>(bc.g, bc.it_end, smem);
+    else if (bc.R == 8) t1_run_chain<8>(bc.g, bc.it_end, smem);
+    else t1_run_chain<16>(bc.g, bc.it_end, smem);
   }
 }
 

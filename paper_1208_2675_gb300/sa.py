@@ -45,6 +45,12 @@ class qap_sa_info(ctypes.Structure):
                 ("smem_bytes", ctypes.c_uint64)]
 
 
+class qap_problem(ctypes.Structure):
+    _fields_ = [("A", _i32p), ("B", _i32p), ("p0", _i32p), ("N", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32), ("sched", qap_schedule),
+                ("seed", ctypes.c_uint64)]
+
+
 # Every symbol include/qap_sa.h declares, with its ctypes signature.
 SIGNATURES = {
     "qap_sa_create": (ctypes.c_int, [_i32p, _i32p, ctypes.c_int32, _i32p,
@@ -65,6 +71,13 @@ SIGNATURES = {
     "qap_sa_delta": (ctypes.c_int, [ctypes.c_void_p, _i32p]),
     "qap_sa_temperature": (ctypes.c_double, [ctypes.c_void_p, ctypes.c_uint64]),
     "qap_sa_destroy": (None, [ctypes.c_void_p]),
+    "qap_batch_create": (ctypes.c_int, [ctypes.POINTER(qap_problem), ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "qap_batch_run": (ctypes.c_int, [ctypes.c_void_p, _u64p]),
+    "qap_batch_result": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _i32p, _i64p, _u64p]),
+    "qap_batch_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.POINTER(qap_sa_info)]),
+    "qap_batch_destroy": (None, [ctypes.c_void_p]),
     "qap_sa_setup_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p]),
@@ -198,6 +211,55 @@ def qap_sa_max_n() -> int:
 
 def qap_sa_strerror(status: int) -> str:
     return lib().qap_sa_strerror(int(status)).decode()
+
+
+def qap_batch_create(problems) -> ctypes.c_void_p:
+    """problems: list of dicts with A, B, p0, t0, tf, total_iters, relative,
+    stream_id, seed.  Host arrays are kept alive for the duration of the call."""
+    keep = []
+    arr = (qap_problem * len(problems))()
+    for i, pr in enumerate(problems):
+        A, B, p0 = _i32(pr["A"]), _i32(pr["B"]), _i32(pr["p0"])
+        keep += [A, B, p0]
+        arr[i].A = A.ctypes.data_as(_i32p)
+        arr[i].B = B.ctypes.data_as(_i32p)
+        arr[i].p0 = p0.ctypes.data_as(_i32p)
+        arr[i].N = len(p0)
+        arr[i].reserved = 0
+        arr[i].sched = make_schedule(pr["t0"], pr["tf"], pr["total_iters"],
+                                     pr.get("relative", True), pr.get("stream_id", 0))
+        arr[i].seed = int(pr.get("seed", 0))
+    h = ctypes.c_void_p()
+    _check(lib().qap_batch_create(arr, len(problems), ctypes.byref(h)), "qap_batch_create")
+    return h
+
+
+def qap_batch_run(h, iters=None) -> None:
+    if iters is None:
+        _check(lib().qap_batch_run(h, None), "qap_batch_run")
+    else:
+        it = np.ascontiguousarray(iters, dtype=np.uint64)
+        _check(lib().qap_batch_run(h, it.ctypes.data_as(_u64p)), "qap_batch_run")
+
+
+def qap_batch_result(h, i: int, N: int):
+    p = np.zeros(N, dtype=np.int32)
+    cost = ctypes.c_int64()
+    acc = ctypes.c_uint64()
+    _check(lib().qap_batch_result(h, int(i), p.ctypes.data_as(_i32p), ctypes.byref(cost),
+                                  ctypes.byref(acc)), "qap_batch_result")
+    return p, cost.value, acc.value
+
+
+def qap_batch_get_info(h, i: int) -> dict:
+    info = qap_sa_info()
+    _check(lib().qap_batch_get_info(h, int(i), ctypes.byref(info)), "qap_batch_get_info")
+    return {name: getattr(info, name) for name, _ in qap_sa_info._fields_}
+
+
+def qap_batch_destroy(h) -> None:
+    if h:
+        lib().qap_batch_destroy(h)
 
 
 # ---- convenience wrapper ----------------------------------------------------- #

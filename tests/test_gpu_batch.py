@@ -1,0 +1,68 @@
+"""Batch of independent chains: every chain's result in the mix equals the
+result of the same chain run alone (single-chain path) and the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_2675_gb300 import instances
+from paper_1208_2675_gb300 import sa
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems(sizes, I, base_seed):
+    probs = []
+    for c, N in enumerate(sizes):
+        A, B, p0 = instances.taixxa_like(int(N), base_seed + c)
+        probs.append(dict(A=A, B=B, p0=p0, t0=0.5, tf=1e-3, total_iters=I,
+                          stream_id=c, seed=base_seed + c))
+    return probs
+
+
+def test_batch_equals_single_chain_and_oracle():
+    sizes = [5, 12, 37, 64, 100, 129, 160, 200, 256, 12, 100, 3, 2, 77, 150, 230]
+    I = 30000
+    probs = _problems(sizes, I, 1000)
+    b = sa.qap_batch_create(probs)
+    try:
+        sa.qap_batch_run(b)  # every chain to its total_iters
+        for c, pr in enumerate(probs):
+            N = len(pr["p0"])
+            p, cost, acc = sa.qap_batch_result(b, c, N)
+            alone = sa.Chain(pr["A"], pr["B"], pr["p0"], t0=0.5, tf=1e-3, total_iters=I,
+                             seed=pr["seed"], stream_id=pr["stream_id"])
+            alone.run(I)
+            p1, cost1, acc1 = alone.result()
+            assert acc == acc1 and cost == cost1 and np.array_equal(p, p1), c
+            if N <= 130:
+                o = oracle.Chain(pr["A"], pr["B"], pr["p0"], t0=0.5, tf=1e-3, total_iters=I,
+                                 seed=pr["seed"], stream=pr["stream_id"])
+                o.run(I)
+                st = o.state()
+                assert acc == st["accepts"] and cost == st["cost"]
+                assert np.array_equal(p, st["p"])
+            assert sa.qap_batch_get_info(b, c)["iterations"] == I
+    finally:
+        sa.qap_batch_destroy(b)
+
+
+def test_batch_run_in_pieces_and_range_check():
+    sizes = [20, 50, 90]
+    I = 20000
+    probs = _problems(sizes, I, 77)
+    b = sa.qap_batch_create(probs)
+    try:
+        sa.qap_batch_run(b, [5000, 7000, 1])
+        sa.qap_batch_run(b, [15000, 13000, 19999])
+        with pytest.raises(sa.QapError) as e:
+            sa.qap_batch_run(b, [1, 0, 0])
+        assert e.value.status == sa.QAP_E_RANGE
+        for c, pr in enumerate(probs):
+            o = oracle.Chain(pr["A"], pr["B"], pr["p0"], t0=0.5, tf=1e-3, total_iters=I,
+                             seed=pr["seed"], stream=pr["stream_id"])
+            o.run(I)
+            st = o.state()
+            p, cost, acc = sa.qap_batch_result(b, c, len(pr["p0"]))
+            assert acc == st["accepts"] and cost == st["cost"] and np.array_equal(p, st["p"])
+    finally:
+        sa.qap_batch_destroy(b)
