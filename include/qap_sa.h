@@ -53,7 +53,7 @@ extern "C" {
 #define QAP_E_CUDA       (-4) /* a CUDA call failed (message via strerror) */
 #define QAP_E_TIMEOUT    (-5) /* a bounded device-side wait expired */
 #define QAP_E_STATE      (-6) /* the device reported an inconsistent state */
-#define QAP_E_UNSUPPORTED (-7) /* N larger than the largest supported tier */
+#define QAP_E_UNSUPPORTED (-7) /* N larger than the largest supported tier (qap_sa_max_n) */
 
 /* ---- cooling schedule ---------------------------------------------------- */
 /* Temperature T of Eq. (2) is lowered after every iteration (section 2.1) by
@@ -129,7 +129,10 @@ QAP_EXPORT int qap_sa_result_device(qap_sa *h, int32_t *p_out, int64_t *cost,
 /* Diagnostics of the current state (after a stream sync). */
 typedef struct qap_sa_info {
   int32_t N;
-  int32_t tier;           /* 1 = one CTA with everything in shared memory   */
+  int32_t tier;           /* 1 = one CTA (Delta in its registers, A and B' in
+                             its shared memory); 2 = a thread-block cluster
+                             (Delta in the cluster's registers, A and B' in
+                             global memory), for N beyond one SM           */
   uint64_t iterations;    /* it: iterations done                            */
   uint64_t accepts;
   int64_t cost;
@@ -211,7 +214,8 @@ QAP_EXPORT int qap_sa_setup_noalloc(const int32_t *A, const int32_t *B, int32_t 
                                     int64_t *cost_out, void *cuda_stream);
 
 /* ---- library ------------------------------------------------------------- */
-/* Largest N any tier supports on the current device (0 if no device).       */
+/* Largest N any tier supports on the current device (0 if no device): about
+ * 276 on one SM, about 1100 on a cluster of up to 16 SMs.                   */
 QAP_EXPORT int32_t qap_sa_max_n(void);
 
 /* Static text for a status code; for QAP_E_CUDA the last CUDA error text of

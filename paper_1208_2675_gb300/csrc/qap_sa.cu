@@ -13,7 +13,7 @@
 #include <new>
 
 #include "qap_sa.h"
-#include "sa_tier1.cuh"
+#include "sa_tier2.cuh"
 
 #include <vector>
 
@@ -140,6 +140,8 @@ struct qap_sa {
   ChainDev dev{};
   T1Layout layout{};
   int R = 4, nthreads = 0;
+  int cluster = 1;      // CTAs per chain (tier 2)
+  int smem_bytes = 0;   // dynamic shared memory of the SA kernel
   unsigned long long it_host = 0;  // iterations enqueued so far
   int tier = 1;
 };
@@ -191,6 +193,78 @@ int max_n_tier1() {
   return lo;
 }
 
+// Tier 2: one chain on a cluster of C CTAs of 640 threads, R = 16 tiles.
+int tier2_cluster(int N) {
+  const int nt = (int)make_tiles(N, kT2R).size();
+  return (nt + kT2Threads - 1) / kT2Threads;
+}
+
+int tier2_tpv(int N, int C) {
+  const int NV = (N + C - 1) / C;
+  int tpv = pow2_floor(kT2Threads / (NV > 0 ? NV : 1));
+  return tpv > 4 ? 4 : (tpv < 1 ? 1 : tpv);
+}
+
+int tier2_fits(int N) {
+  const int C = tier2_cluster(N);
+  if (C < 2 || C > kT2MaxCluster) return 0;
+  const int NV = (N + C - 1) / C;
+  const int vslots = (kT2Threads / 32) * (32 / tier2_tpv(N, C));
+  if (NV > 2 * vslots) return 0;
+  if (t2_layout(N).bytes > device_smem_optin()) return 0;
+  static int ok_for[kT2MaxCluster + 1] = {0};  // 0 unknown, 1 yes, -1 no
+  if (ok_for[C] == 0) {
+    cudaFuncSetAttribute(sa_tier2_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(sa_tier2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         t2_layout(N).bytes);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kT2Threads);
+    cfg.dynamicSmemBytes = t2_layout(N).bytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    ok_for[C] = (cudaOccupancyMaxActiveClusters(&n, sa_tier2_kernel, &cfg) == cudaSuccess &&
+                 n >= 1) ? 1 : -1;
+    cudaGetLastError();
+  }
+  return ok_for[C] > 0;
+}
+
+int max_n_any() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  int best = max_n_tier1();
+  for (int N = best + 1; N <= 2048; ++N) {
+    if (tier2_cluster(N) > kT2MaxCluster) break;
+    if (tier2_fits(N)) best = N;
+  }
+  cached = best;
+  return best;
+}
+
+cudaError_t launch_tier2(const ChainDev &g, unsigned long long it_end, int C,
+                         int smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kT2Threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sa_tier2_kernel, g, it_end);
+}
+
 // Common body of the two create entry points; A32/B32/p032 are device
 // pointers that stay valid for the duration of the call.
 int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
@@ -228,7 +302,8 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   CKF(cudaMalloc(&h->d, sizeof(int) * N));
   CKF(cudaMalloc(&h->st, sizeof(ChainStatus)));
   CKF(cudaMalloc(&h->P, sizeof(double) * 8 * 256));
-  const std::vector<int> tiles = make_tiles(N, tile_rows(N));
+  h->tier = N <= max_n_tier1() ? 1 : 2;
+  const std::vector<int> tiles = make_tiles(N, h->tier == 1 ? tile_rows(N) : kT2R);
   CKF(cudaMalloc(&h->tiles, sizeof(int) * (tiles.size() ? tiles.size() : 1)));
   CKF(cudaMemcpyAsync(h->tiles, tiles.data(), sizeof(int) * tiles.size(),
                       cudaMemcpyHostToDevice, stream));
@@ -292,13 +367,20 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   g.N = N;
   g.S = S;
   g.M = M;
-  h->R = tile_rows(N);
-  h->nthreads = tier1_threads(N, (int)tiles.size());
   g.ntiles = (int)tiles.size();
   g.tiles = h->tiles;
-  g.tpv = pow2_floor(h->nthreads / N);
-  if (g.tpv > 4) g.tpv = 4;  // >= 8 lanes per slice keep the 16-byte loads
-                             // of eight consecutive rows conflict-free
+  if (h->tier == 1) {
+    h->R = tile_rows(N);
+    h->nthreads = tier1_threads(N, (int)tiles.size());
+    g.tpv = pow2_floor(h->nthreads / N);
+    if (g.tpv > 4) g.tpv = 4;  // >= 8 lanes per slice keep the 16-byte loads
+                               // of eight consecutive rows conflict-free
+  } else {
+    h->R = kT2R;
+    h->nthreads = kT2Threads;
+    h->cluster = tier2_cluster(N);
+    g.tpv = tier2_tpv(N, h->cluster);
+  }
   g.A = h->A8;
   g.Bp = h->Bp8;
   g.delta = h->delta;
@@ -316,7 +398,11 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   // product's drift from T0 alpha^it, and the exponent's rounding.
   g.mrel = (float)(2e-5 + 2e-7 * fabs(l2r) + 8.0 * (double)sc->total_iters * 0x1p-53);
   h->layout = t1_layout(N, S);
-  if (h->R == 4)
+  h->smem_bytes = h->tier == 1 ? h->layout.bytes : t2_layout(N).bytes;
+  if (h->tier == 2)
+    CKF(cudaFuncSetAttribute(sa_tier2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             h->smem_bytes));
+  else if (h->R == 4)
     CKF(cudaFuncSetAttribute(sa_tier1_kernel<4>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, h->layout.bytes));
   else if (h->R == 8)
@@ -341,9 +427,8 @@ int validate_args(const void *A, const void *B, int32_t N, const void *p0,
   if (!(sc->t0 > 0.0) || !(sc->tf > 0.0) || !isfinite(sc->t0) || !isfinite(sc->tf))
     return QAP_E_INVAL;
   if (sc->flags & ~QAP_T_RELATIVE) return QAP_E_INVAL;
-  const int nmax = max_n_tier1();
-  if (nmax == 0) return QAP_E_CUDA;
-  if (N > nmax) return QAP_E_UNSUPPORTED;
+  if (max_n_tier1() == 0) return QAP_E_CUDA;
+  if (N > max_n_any()) return QAP_E_UNSUPPORTED;
   return QAP_OK;
 }
 
@@ -425,7 +510,10 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
   while (cur < end) {
     unsigned long long stop = cur + chunk_iters();
     if (stop > end) stop = end;
-    if (h->R == 4)
+    if (h->tier == 2) {
+      cudaError_t e2 = launch_tier2(h->dev, stop, h->cluster, h->smem_bytes, h->stream);
+      if (e2 != cudaSuccess) return cuda_fail(e2, "sa_tier2_kernel launch");
+    } else if (h->R == 4)
       sa_tier1_kernel<4><<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
     else if (h->R == 8)
       sa_tier1_kernel<8><<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
@@ -501,7 +589,7 @@ int qap_sa_get_info(qap_sa *h, qap_sa_info *out) {
   out->Tf = h->sched.Tf;
   out->alpha = h->sched.alpha;
   out->total_iters = h->sched.I;
-  out->smem_bytes = (uint64_t)h->layout.bytes;
+  out->smem_bytes = (uint64_t)h->smem_bytes;
   return st.error ? QAP_E_STATE : QAP_OK;
 }
 
@@ -520,7 +608,7 @@ double qap_sa_temperature(const qap_sa *h, uint64_t it) {
 
 void qap_sa_destroy(qap_sa *h) { free_handle(h); }
 
-int32_t qap_sa_max_n(void) { return max_n_tier1(); }
+int32_t qap_sa_max_n(void) { return max_n_any(); }
 
 const char *qap_sa_strerror(int status) {
   switch (status) {
@@ -545,12 +633,14 @@ struct qap_batch {
   int count = 0;
   std::vector<qap_sa *> h;
   std::vector<BatchChain> chains;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr, stream2 = nullptr;
   BatchChain *d_chains = nullptr;
-  int *d_order = nullptr;
-  int *d_counter = nullptr;
-  int smem = 0;
-  int grid = 0;
+  int *d_order = nullptr;    // tier-1 chains (one CTA each), then tier-2 chains
+  int *d_counter = nullptr;  // [0]: next tier-1 chain, [1]: next tier-2 chain
+  int n1 = 0, n2 = 0;        // chains per tier
+  int smem = 0, smem2 = 0;
+  int grid = 0, cluster2 = 0, grid2 = 0;
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -565,6 +655,9 @@ void free_batch(qap_batch *b) {
   cudaFree(b->d_order);
   cudaFree(b->d_counter);
   if (b->stream) cudaStreamDestroy(b->stream);
+  if (b->stream2) cudaStreamDestroy(b->stream2);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
   delete b;
 }
 
@@ -600,16 +693,27 @@ int qap_batch_create(const qap_problem *probs, int32_t count, qap_batch **out) {
     bc.it_end = 0;
     bc.R = h->R;
     b->chains.push_back(bc);
-    if (h->layout.bytes > b->smem) b->smem = h->layout.bytes;
+    if (h->tier == 1) {
+      ++b->n1;
+      if (h->smem_bytes > b->smem) b->smem = h->smem_bytes;
+    } else {
+      ++b->n2;
+      if (h->smem_bytes > b->smem2) b->smem2 = h->smem_bytes;
+      if (h->cluster > b->cluster2) b->cluster2 = h->cluster;
+    }
   }
-  // work list: most work first (N^2 I)
+  // work lists: tier-1 chains then tier-2 chains, each most work (N^2 I) first
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int x, int y) {
+    if (b->h[x]->tier != b->h[y]->tier) return b->h[x]->tier < b->h[y]->tier;
     const double wx = (double)b->h[x]->N * b->h[x]->N * (double)b->h[x]->sched.I;
     const double wy = (double)b->h[y]->N * b->h[y]->N * (double)b->h[y]->sched.I;
     return wx > wy;
   });
+  double work1 = 0, work2 = 0;
+  for (qap_sa *h : b->h)
+    (h->tier == 1 ? work1 : work2) += (double)h->N * h->N * (double)h->sched.I;
   int dev = 0, sms = 0;
   auto fail = [&](cudaError_t err, const char *what) {
     int rc = cuda_fail(err, what);
@@ -619,27 +723,78 @@ int qap_batch_create(const qap_problem *probs, int32_t count, qap_batch **out) {
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return fail(e, "cudaGetDevice");
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return fail(e, "cudaDeviceGetAttribute");
-  b->grid = count < sms ? count : sms;
+  // SMs for the cluster branch in proportion to its share of the work.
+  int sm2 = 0;
+  if (b->n2) {
+    const int C = b->cluster2;
+    sm2 = (int)((double)sms * work2 / (work1 + work2));
+    if (b->n1 == 0) sm2 = sms;
+    sm2 = (sm2 / C) * C;
+    if (sm2 < C) sm2 = C;
+    if (sm2 > b->n2 * C) sm2 = b->n2 * C;
+    if (b->n1 && sm2 > sms - 1) sm2 = ((sms - 1) / C) * C;
+    b->grid2 = sm2;
+  }
+  b->grid = b->n1 < sms - sm2 ? b->n1 : sms - sm2;
+  if (b->n1 && b->grid < 1) b->grid = 1;
   if ((e = cudaMalloc(&b->d_chains, sizeof(BatchChain) * count)) != cudaSuccess)
     return fail(e, "cudaMalloc");
   if ((e = cudaMalloc(&b->d_order, sizeof(int) * count)) != cudaSuccess)
     return fail(e, "cudaMalloc");
-  if ((e = cudaMalloc(&b->d_counter, sizeof(int))) != cudaSuccess)
+  if ((e = cudaMalloc(&b->d_counter, 2 * sizeof(int))) != cudaSuccess)
     return fail(e, "cudaMalloc");
+  if ((e = cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail(e, "cudaStreamCreate");
+  if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(e, "cudaEventCreate");
+  if ((e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(e, "cudaEventCreate");
   if ((e = cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * count,
                            cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
     return fail(e, "cudaMemcpyAsync");
-  if ((e = cudaFuncSetAttribute(sa_batch_kernel,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                b->smem)) != cudaSuccess)
+  if (b->n1 && (e = cudaFuncSetAttribute(sa_batch_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          b->smem)) != cudaSuccess)
     return fail(e, "cudaFuncSetAttribute");
-  // The whole run is one graph: reset the work counter, one persistent launch.
+  if (b->n2) {
+    if ((e = cudaFuncSetAttribute(sa_tier2_batch_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  b->smem2)) != cudaSuccess)
+      return fail(e, "cudaFuncSetAttribute");
+    if ((e = cudaFuncSetAttribute(sa_tier2_batch_kernel,
+                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+      return fail(e, "cudaFuncSetAttribute");
+  }
+  // The whole run is one graph: reset the work counters, then two persistent
+  // launches side by side -- one CTA per chain for chains that fit one SM,
+  // clusters for the others.
   cudaGraph_t graph = nullptr;
   if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     return fail(e, "cudaStreamBeginCapture");
-  cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
-  sa_batch_kernel<<<b->grid, kBatchThreads, b->smem, b->stream>>>(
-      b->d_chains, b->d_order, count, b->d_counter);
+  cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), b->stream);
+  if (b->n2) {
+    cudaEventRecord(b->fork, b->stream);
+    cudaStreamWaitEvent(b->stream2, b->fork, 0);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = b->cluster2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(b->grid2);
+    cfg.blockDim = dim3(kT2Threads);
+    cfg.dynamicSmemBytes = b->smem2;
+    cfg.stream = b->stream2;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, sa_tier2_batch_kernel, (const BatchChain *)b->d_chains,
+                       (const int *)(b->d_order + b->n1), b->n2, b->d_counter + 1);
+    cudaEventRecord(b->join, b->stream2);
+  }
+  if (b->n1)
+    sa_batch_kernel<<<b->grid, kBatchThreads, b->smem, b->stream>>>(
+        b->d_chains, b->d_order, b->n1, b->d_counter);
+  if (b->n2) cudaStreamWaitEvent(b->stream, b->join, 0);
   if ((e = cudaStreamEndCapture(b->stream, &graph)) != cudaSuccess)
     return fail(e, "cudaStreamEndCapture");
   e = cudaGraphInstantiate(&b->exec, graph, 0);

@@ -46,6 +46,31 @@ def test_batch_equals_single_chain_and_oracle():
         sa.qap_batch_destroy(b)
 
 
+def test_batch_mixes_one_sm_chains_and_cluster_chains():
+    """N up to 300 (the batch workload's range): chains above one SM's limit run
+    on clusters in a second persistent launch of the same graph."""
+    sizes = [290, 20, 300, 150, 277, 64, 280]
+    I = 6000
+    probs = _problems(sizes, I, 500)
+    b = sa.qap_batch_create(probs)
+    try:
+        sa.qap_batch_run(b)
+        tiers = set()
+        for c, pr in enumerate(probs):
+            N = len(pr["p0"])
+            p, cost, acc = sa.qap_batch_result(b, c, N)
+            tiers.add(sa.qap_batch_get_info(b, c)["tier"])
+            o = oracle.Chain(pr["A"], pr["B"], pr["p0"], t0=0.5, tf=1e-3, total_iters=I,
+                             seed=pr["seed"], stream=pr["stream_id"])
+            o.run(I)
+            st = o.state()
+            assert acc == st["accepts"] and cost == st["cost"], c
+            assert np.array_equal(p, st["p"])
+        assert tiers == {1, 2}
+    finally:
+        sa.qap_batch_destroy(b)
+
+
 def test_batch_run_in_pieces_and_range_check():
     sizes = [20, 50, 90]
     I = 20000

@@ -236,3 +236,27 @@ def test_n256_workload_prefix_matches_oracle():
                                      oracle_iters=100000)
     assert os_["accepts"] > 10000
     assert_same(gs, os_, gd, od)
+
+
+@pytest.mark.parametrize("N,I,iters,seed", [(277, 10 ** 7, 40000, 31), (300, 10 ** 7, 30000, 32),
+                                            (513, 10 ** 8, 8000, 33)])
+def test_cluster_tier_matches_oracle(N, I, iters, seed):
+    """Sizes beyond one SM: the chain runs on a thread-block cluster."""
+    A, B, p0 = instances.taixxa_like(N, seed)
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=I, seed=seed,
+                                     stream=seed, oracle_iters=iters)
+    assert g.info()["tier"] == 2
+    assert os_["accepts"] > 500
+    assert_same(gs, os_, gd, od)
+
+
+def test_n1024_grid_workload_prefix_matches_oracle():
+    """N = 1024: B = Manhattan distances on a 32 x 32 grid, A with 30 % nonzeros
+    in [1, 10], I = 2e9 schedule; the first 4000 iterations against the oracle,
+    run in two pieces."""
+    A, B, p0 = instances.grid_instance(32, 1)
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=2 * 10 ** 9, seed=1,
+                                     oracle_iters=4000, splits=[1500, 2500])
+    assert g.info()["tier"] == 2
+    assert os_["accepts"] > 300
+    assert_same(gs, os_, gd, od)
