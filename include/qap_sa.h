@@ -188,6 +188,47 @@ QAP_EXPORT int qap_batch_result(qap_batch *b, int32_t i, int32_t *p_out,
 QAP_EXPORT int qap_batch_get_info(qap_batch *b, int32_t i, qap_sa_info *out);
 QAP_EXPORT void qap_batch_destroy(qap_batch *b);
 
+/* ---- serving: continuous batching of solve requests -----------------------
+ * A worker thread of the library admits submitted requests in arrival order as
+ * soon as SMs (one per chain, or the chain's cluster size for large N) and
+ * device memory (the budget) are free, runs each on its own stream, and keeps
+ * every chain's state on the device until it finishes.  Requests that arrive
+ * while others run are admitted as slots free up and overlap with them.  The
+ * paper has no counterpart; each request's result equals qap_sa_run's for the
+ * same problem.                                                               */
+typedef struct qap_server_cfg {
+  int32_t max_sms;          /* SMs the server may fill (0 = all)               */
+  uint32_t reserved;        /* must be 0                                       */
+  uint64_t mem_budget_bytes;/* device bytes for chains (0 = 80 % of free)      */
+} qap_server_cfg;
+
+typedef struct qap_result {
+  int32_t done;       /* 1 once the request has finished                      */
+  int32_t status;     /* its status code (valid when done)                    */
+  int64_t cost;       /* Eq. (1) of the final assignment                      */
+  uint64_t accepts;
+  uint64_t iterations;
+  double queue_s;     /* seconds from submit to admission                     */
+  double latency_s;   /* seconds from submit to completion                    */
+} qap_result;
+
+typedef struct qap_server qap_server; /* opaque; freed by qap_server_stop */
+
+/* Starts the worker on the current device; cfg may be NULL.                  */
+QAP_EXPORT int qap_server_start(const qap_server_cfg *cfg, qap_server **out);
+/* Queues `iters` iterations of problem q (inputs copied during the call;
+ * iters <= q->sched.total_iters); *ticket identifies the request.            */
+QAP_EXPORT int qap_server_submit(qap_server *s, const qap_problem *q,
+                                 uint64_t iters, uint64_t *ticket);
+/* Non-blocking: fills *out (out->done = 0 while pending); when done and p_out
+ * is not NULL, copies the final assignment (N int32) into it.               */
+QAP_EXPORT int qap_server_poll(qap_server *s, uint64_t ticket, qap_result *out,
+                               int32_t *p_out);
+/* Largest number of requests that were on the device at the same time.     */
+QAP_EXPORT int qap_server_max_running(qap_server *s);
+/* Finishes every queued and running request, stops the worker, frees all.   */
+QAP_EXPORT int qap_server_stop(qap_server *s);
+
 /* ---- set-up without allocation ---------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot call cudaMalloc -- programs whose device memory belongs to another

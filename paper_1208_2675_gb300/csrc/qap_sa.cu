@@ -13,6 +13,7 @@
 #include <new>
 
 #include "qap_sa.h"
+#include "qap_internal.h"
 #include "sa_tier2.cuh"
 
 #include <vector>
@@ -943,4 +944,18 @@ extern "C" int qap_sa_setup_noalloc(const int32_t *A, const int32_t *B,
   if (so_h.flags & (kFlagAsym | kFlagDiag | kFlagPerm)) return QAP_E_INVAL;
   if (so_h.flags & (kFlagRangeA | kFlagRangeB)) return QAP_E_RANGE;
   return QAP_OK;
+}
+
+// ------------------------------------------------------------------------- //
+// Hooks for the other translation units (qap_internal.h).
+// ------------------------------------------------------------------------- //
+cudaStream_t qapsa_handle_stream(qap_sa *h) { return h ? h->stream : nullptr; }
+
+int qapsa_sms_for(int N) { return N <= max_n_tier1() ? 1 : tier2_cluster(N); }
+
+size_t qapsa_bytes_for(int N) {
+  const size_t S = (size_t)row_stride(N), M = (size_t)N * (N - 1) / 2;
+  const size_t state = 2 * (size_t)N * S + 4 * M + 8 * (size_t)N + 16384 + 4096;
+  const size_t setup_peak = 3 * 4 * (size_t)N * N + 4 * (size_t)N;  // A, B, G staging
+  return state + setup_peak;
 }

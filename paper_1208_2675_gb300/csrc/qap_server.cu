@@ -1,0 +1,256 @@
+// qap_server.cu -- continuous-batching solve server of libqapsa (host runtime).
+//
+// A worker thread owns the GPU side.  Submitted requests wait in a FIFO; the
+// worker admits the head of the queue as soon as enough SMs (one per chain, or
+// the cluster size for large N) and enough of the device-memory budget are
+// free, sets the chain up on its own stream and enqueues its whole run.  Many
+// chains are on the device at once and their kernels overlap; a request that
+// arrives while others run is admitted the moment a slot and memory free up.
+// Each chain's Delta, B', p and counters stay on the device from set-up to the
+// end of its run.  Completion is detected with an event per chain; the result
+// is read back and the chain's memory freed.  The paper has no counterpart (it
+// runs one chain); a chain's trajectory is the one qap_sa_run gives it alone.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "qap_internal.h"
+#include "qap_sa.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket = 0;
+  int32_t N = 0;
+  std::vector<int32_t> A, B, p0;  // freed once the chain is set up
+  qap_schedule sched{};
+  uint64_t seed = 0, iters = 0;
+  int sms = 1;
+  size_t bytes = 0;
+  Clock::time_point t_submit, t_start, t_done;
+  qap_sa *h = nullptr;
+  cudaEvent_t done_ev = nullptr;
+  bool done = false;
+  int32_t status = QAP_OK;
+  int64_t cost = 0;
+  uint64_t accepts = 0;
+  std::vector<int32_t> p;
+};
+
+}  // namespace
+
+struct qap_server {
+  qap_server_cfg cfg{};
+  int device = 0;
+  int max_sms = 0;
+  size_t budget = 0;
+  std::mutex mu;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::unordered_map<uint64_t, std::shared_ptr<Request>> by_ticket;
+  std::vector<std::shared_ptr<Request>> running;  // worker thread only
+  int sms_used = 0;
+  size_t bytes_used = 0;
+  uint64_t next_ticket = 1;
+  std::atomic<bool> stopping{false};
+  std::atomic<int> max_running{0};
+  std::thread worker;
+};
+
+namespace {
+
+void finish(qap_server *s, const std::shared_ptr<Request> &r) {
+  std::vector<int32_t> p(r->N);
+  int64_t cost = 0;
+  uint64_t acc = 0;
+  int st = qap_sa_sync(r->h);
+  if (st == QAP_OK) st = qap_sa_result(r->h, p.data(), &cost, &acc);
+  qap_sa_destroy(r->h);
+  r->h = nullptr;
+  cudaEventDestroy(r->done_ev);
+  r->done_ev = nullptr;
+  std::lock_guard<std::mutex> lock(s->mu);
+  r->p.swap(p);
+  r->cost = cost;
+  r->accepts = acc;
+  r->status = st;
+  r->t_done = Clock::now();
+  r->done = true;
+  s->sms_used -= r->sms;
+  s->bytes_used -= r->bytes;
+}
+
+// Sets the chain up on its own stream and enqueues its whole run; false if
+// the request failed (its status is recorded).
+bool launch(qap_server *s, const std::shared_ptr<Request> &r) {
+  qap_sa *h = nullptr;
+  int st = qap_sa_create(r->A.data(), r->B.data(), r->N, r->p0.data(), &r->sched,
+                         r->seed, &h);
+  if (st == QAP_OK) st = qap_sa_run_async(h, r->iters);
+  cudaEvent_t ev = nullptr;
+  if (st == QAP_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+    st = QAP_E_CUDA;
+  if (st == QAP_OK && cudaEventRecord(ev, qapsa_handle_stream(h)) != cudaSuccess)
+    st = QAP_E_CUDA;
+  std::vector<int32_t>().swap(r->A);
+  std::vector<int32_t>().swap(r->B);
+  if (st != QAP_OK) {
+    if (ev) cudaEventDestroy(ev);
+    qap_sa_destroy(h);
+    std::lock_guard<std::mutex> lock(s->mu);
+    r->status = st;
+    r->t_done = Clock::now();
+    r->done = true;
+    s->sms_used -= r->sms;
+    s->bytes_used -= r->bytes;
+    return false;
+  }
+  r->h = h;
+  r->done_ev = ev;
+  return true;
+}
+
+void worker_main(qap_server *s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    bool progress = false;
+    // ---- completions ----
+    for (size_t i = 0; i < s->running.size();) {
+      const std::shared_ptr<Request> &r = s->running[i];
+      if (cudaEventQuery(r->done_ev) == cudaErrorNotReady) {
+        ++i;
+        continue;
+      }
+      finish(s, r);
+      s->running[i] = s->running.back();
+      s->running.pop_back();
+      progress = true;
+    }
+    // ---- admissions: FIFO, as SMs and memory allow ----
+    for (;;) {
+      std::shared_ptr<Request> r;
+      {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->queue.empty()) break;
+        std::shared_ptr<Request> &head = s->queue.front();
+        const bool fits = s->sms_used + head->sms <= s->max_sms &&
+                          s->bytes_used + head->bytes <= s->budget;
+        if (!fits && !s->running.empty()) break;  // wait for a slot to free up
+        r = head;
+        s->queue.pop_front();
+        s->sms_used += r->sms;
+        s->bytes_used += r->bytes;
+        r->t_start = Clock::now();
+      }
+      if (launch(s, r)) {
+        s->running.push_back(r);
+        const int n = (int)s->running.size();
+        if (n > s->max_running.load()) s->max_running.store(n);
+      }
+      progress = true;
+    }
+    if (!progress) {
+      bool idle;
+      {
+        std::lock_guard<std::mutex> lock(s->mu);
+        idle = s->queue.empty() && s->running.empty();
+      }
+      if (idle && s->stopping.load()) return;
+      std::this_thread::sleep_for(std::chrono::microseconds(idle ? 200 : 20));
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int qap_server_start(const qap_server_cfg *cfg, qap_server **out) {
+  if (!out) return QAP_E_INVAL;
+  *out = nullptr;
+  qap_server *s = new (std::nothrow) qap_server();
+  if (!s) return QAP_E_NOMEM;
+  if (cfg) s->cfg = *cfg;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    return QAP_E_CUDA;
+  }
+  int sms = 0;
+  size_t free_b = 0, total_b = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
+      cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    delete s;
+    return QAP_E_CUDA;
+  }
+  s->max_sms = (s->cfg.max_sms > 0 && s->cfg.max_sms < sms) ? s->cfg.max_sms : sms;
+  s->budget = s->cfg.mem_budget_bytes ? (size_t)s->cfg.mem_budget_bytes
+                                      : (size_t)(0.8 * (double)free_b);
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return QAP_OK;
+}
+
+int qap_server_submit(qap_server *s, const qap_problem *q, uint64_t iters,
+                      uint64_t *ticket) {
+  if (!s || !q || !ticket || !q->A || !q->B || !q->p0 || q->N < 2) return QAP_E_INVAL;
+  if (s->stopping.load()) return QAP_E_STATE;
+  if (iters > q->sched.total_iters) return QAP_E_RANGE;
+  if (q->N > qap_sa_max_n()) return QAP_E_UNSUPPORTED;
+  auto r = std::make_shared<Request>();
+  const size_t nn = (size_t)q->N * q->N;
+  r->N = q->N;
+  r->A.assign(q->A, q->A + nn);
+  r->B.assign(q->B, q->B + nn);
+  r->p0.assign(q->p0, q->p0 + q->N);
+  r->sched = q->sched;
+  r->seed = q->seed;
+  r->iters = iters;
+  r->sms = qapsa_sms_for(q->N);
+  r->bytes = qapsa_bytes_for(q->N);
+  r->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lock(s->mu);
+  r->ticket = s->next_ticket++;
+  s->queue.push_back(r);
+  s->by_ticket[r->ticket] = r;
+  *ticket = r->ticket;
+  return QAP_OK;
+}
+
+int qap_server_poll(qap_server *s, uint64_t ticket, qap_result *out, int32_t *p_out) {
+  if (!s || !out) return QAP_E_INVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->by_ticket.find(ticket);
+  if (it == s->by_ticket.end()) return QAP_E_INVAL;
+  const Request &r = *it->second;
+  out->done = r.done ? 1 : 0;
+  out->status = r.status;
+  if (!r.done) return QAP_OK;
+  out->cost = r.cost;
+  out->accepts = r.accepts;
+  out->iterations = r.iters;
+  out->queue_s = std::chrono::duration<double>(r.t_start - r.t_submit).count();
+  out->latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
+  if (p_out && !r.p.empty()) std::copy(r.p.begin(), r.p.end(), p_out);
+  return QAP_OK;
+}
+
+int qap_server_max_running(qap_server *s) { return s ? s->max_running.load() : 0; }
+
+int qap_server_stop(qap_server *s) {
+  if (!s) return QAP_E_INVAL;
+  s->stopping.store(true);
+  if (s->worker.joinable()) s->worker.join();
+  delete s;
+  return QAP_OK;
+}
+
+}  // extern "C"

@@ -51,6 +51,18 @@ class qap_problem(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class qap_server_cfg(ctypes.Structure):
+    _fields_ = [("max_sms", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("mem_budget_bytes", ctypes.c_uint64)]
+
+
+class qap_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("cost", ctypes.c_int64), ("accepts", ctypes.c_uint64),
+                ("iterations", ctypes.c_uint64), ("queue_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double)]
+
+
 # Every symbol include/qap_sa.h declares, with its ctypes signature.
 SIGNATURES = {
     "qap_sa_create": (ctypes.c_int, [_i32p, _i32p, ctypes.c_int32, _i32p,
@@ -78,6 +90,14 @@ SIGNATURES = {
     "qap_batch_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
                                           ctypes.POINTER(qap_sa_info)]),
     "qap_batch_destroy": (None, [ctypes.c_void_p]),
+    "qap_server_start": (ctypes.c_int, [ctypes.POINTER(qap_server_cfg),
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "qap_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qap_problem),
+                                         ctypes.c_uint64, _u64p]),
+    "qap_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64,
+                                       ctypes.POINTER(qap_result), _i32p]),
+    "qap_server_max_running": (ctypes.c_int, [ctypes.c_void_p]),
+    "qap_server_stop": (ctypes.c_int, [ctypes.c_void_p]),
     "qap_sa_setup_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p]),
@@ -260,6 +280,59 @@ def qap_batch_get_info(h, i: int) -> dict:
 def qap_batch_destroy(h) -> None:
     if h:
         lib().qap_batch_destroy(h)
+
+
+def _problem_struct(pr, keep):
+    A, B, p0 = _i32(pr["A"]), _i32(pr["B"]), _i32(pr["p0"])
+    keep += [A, B, p0]
+    q = qap_problem()
+    q.A = A.ctypes.data_as(_i32p)
+    q.B = B.ctypes.data_as(_i32p)
+    q.p0 = p0.ctypes.data_as(_i32p)
+    q.N = len(p0)
+    q.reserved = 0
+    q.sched = make_schedule(pr["t0"], pr["tf"], pr["total_iters"], pr.get("relative", True),
+                            pr.get("stream_id", 0))
+    q.seed = int(pr.get("seed", 0))
+    return q
+
+
+def qap_server_start(max_sms: int = 0, mem_budget_bytes: int = 0) -> ctypes.c_void_p:
+    cfg = qap_server_cfg(int(max_sms), 0, int(mem_budget_bytes))
+    h = ctypes.c_void_p()
+    _check(lib().qap_server_start(ctypes.byref(cfg), ctypes.byref(h)), "qap_server_start")
+    return h
+
+
+def qap_server_submit(h, problem: dict, iters: int) -> int:
+    keep = []
+    q = _problem_struct(problem, keep)
+    t = ctypes.c_uint64()
+    _check(lib().qap_server_submit(h, ctypes.byref(q), int(iters), ctypes.byref(t)),
+           "qap_server_submit")
+    return t.value
+
+
+def qap_server_poll(h, ticket: int, N: int):
+    """Returns None while pending, else a dict with the result and p."""
+    res = qap_result()
+    p = np.zeros(N, dtype=np.int32)
+    _check(lib().qap_server_poll(h, int(ticket), ctypes.byref(res), p.ctypes.data_as(_i32p)),
+           "qap_server_poll")
+    if not res.done:
+        return None
+    out = {name: getattr(res, name) for name, _ in qap_result._fields_}
+    out["p"] = p
+    return out
+
+
+def qap_server_max_running(h) -> int:
+    return int(lib().qap_server_max_running(h))
+
+
+def qap_server_stop(h) -> None:
+    if h:
+        _check(lib().qap_server_stop(h), "qap_server_stop")
 
 
 # ---- convenience wrapper ----------------------------------------------------- #
