@@ -30,6 +30,19 @@ WORKLOADS = {
                  desc="single chain, N=100, A and B symmetric uniform int [0,99], "
                       "zero diagonal, random p0, geometric cooling "
                       "T0=0.5*mean|Delta0|, Tf=1e-3*T0, I=1e8"),
+    "n256": dict(N=256, I=10 ** 9, seed=1,
+                 desc="single chain, N=256, A and B symmetric uniform int [0,99], "
+                      "zero diagonal, random p0, geometric cooling "
+                      "T0=0.5*mean|Delta0|, Tf=1e-3*T0, I=1e9"),
+    "batch512": dict(count=512, n_lo=20, n_hi=300, I=10 ** 7, seed=4,
+                     desc="512 independent chains, N ~ U{20..300}, uniform symmetric "
+                          "int [0,99] instances (seed 1000+c, Philox stream c), "
+                          "I=1e7 each, one persistent graph-captured launch"),
+    "serve": dict(count=100, rates=(100, 1000, 5000), n_lo=30, n_hi=600,
+                  i_lo=1e6, i_hi=1e8, seed=5,
+                  desc="Poisson solve requests, N log-uniform [30,600], I log-uniform "
+                       "[1e6,1e8], uniform symmetric int [0,99] instances, continuous "
+                       "batching; a bounded sample of 100 requests per rate"),
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 bytes
 
@@ -314,6 +327,134 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- #
+# batch of independent chains (one persistent graph-captured launch)
+# --------------------------------------------------------------------------- #
+def _batch_problems(wl):
+    from paper_1208_2675_gb300 import instances
+    sizes = instances.batch_sizes(wl["count"], wl["n_lo"], wl["n_hi"], wl["seed"])
+    probs = []
+    for c, N in enumerate(sizes):
+        A, B, p0 = instances.taixxa_like(int(N), 1000 + c)
+        probs.append(dict(A=A, B=B, p0=p0, t0=0.5, tf=1e-3, total_iters=wl["I"],
+                          stream_id=c, seed=1000 + c))
+    return probs
+
+
+def run_batch(args, rank, world, local_rank):
+    import torch
+    from paper_1208_2675_gb300 import sa
+    wl = WORKLOADS["batch512"]
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    probs = _batch_problems(wl)
+    I = wl["I"]
+
+    def step():
+        t0 = time.perf_counter()
+        b = sa.qap_batch_create(probs)
+        t1 = time.perf_counter()
+        sa.qap_batch_run(b)
+        t2 = time.perf_counter()
+        acc = sum(sa.qap_batch_result(b, c, len(pr["p0"]))[2] for c, pr in enumerate(probs))
+        sa.qap_batch_destroy(b)
+        return t2 - t0, t2 - t1, acc
+
+    for _ in range(args.warmup):
+        step()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    res = [step() for _ in range(args.steps)]
+    clk = clocks.stop()
+    t_step = statistics.mean(r[0] for r in res)
+    t_run = statistics.mean(r[1] for r in res)
+    # the plain single-chain path on the same GPU: chains one after another
+    single = []
+    for pr in probs[:6]:
+        h = sa.Chain(pr["A"], pr["B"], pr["p0"], t0=0.5, tf=1e-3, total_iters=I,
+                     seed=pr["seed"], stream_id=pr["stream_id"])
+        t = time.perf_counter()
+        h.run(I)
+        single.append((time.perf_counter() - t, len(pr["p0"])))
+        h.close()
+    n = len(probs)
+    per_chain = statistics.mean(t for t, _ in single)
+    line = {
+        "metric": "batched_chains_per_sec", "value": world * n / t_step, "unit": "chains/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded Taixxa-like instances)",
+        "config": {"workload": wl["desc"], "chains": n, "I": I,
+                   "sizes": "N ~ U{20..300}", "parallelism": f"replicas x{world}"},
+        "run_only_chains_per_sec": n / t_run,
+        "iterations_per_sec": n * I / t_step,
+        "accept_rate": statistics.mean(r[2] for r in res) / (n * I),
+        "single_chain_path": {"chains_per_sec": 1.0 / per_chain,
+                              "sample": f"first {len(single)} chains run one after another "
+                                        f"with qap_sa_run (N = {[m for _, m in single]})"},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- #
+# serving: Poisson request streams through the continuous-batching server
+# --------------------------------------------------------------------------- #
+def run_serve(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1208_2675_gb300 import instances, sa
+    wl = WORKLOADS["serve"]
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    sa.lib()
+    out = []
+    for rate in wl["rates"]:
+        arrival, Ns, Is = instances.request_mix(wl["count"], rate, wl["n_lo"], wl["n_hi"],
+                                                wl["i_lo"], wl["i_hi"], wl["seed"] + rate)
+        reqs = []
+        for k in range(wl["count"]):
+            A, B, p0 = instances.taixxa_like(int(Ns[k]), 7000 + k)
+            reqs.append(dict(A=A, B=B, p0=p0, t0=0.5, tf=1e-3, total_iters=int(Is[k]),
+                             stream_id=k, seed=7000 + k))
+        srv = sa.qap_server_start()
+        t_start = time.perf_counter()
+        tickets = []
+        for k, pr in enumerate(reqs):
+            delay = t_start + arrival[k] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(sa.qap_server_submit(srv, pr, pr["total_iters"]))
+        done = [None] * len(reqs)
+        while any(d is None for d in done):
+            for k, t in enumerate(tickets):
+                if done[k] is None:
+                    done[k] = sa.qap_server_poll(srv, t, len(reqs[k]["p0"]))
+            time.sleep(0.002)
+        t_end = time.perf_counter()
+        maxrun = sa.qap_server_max_running(srv)
+        sa.qap_server_stop(srv)
+        lat = np.array([d["latency_s"] for d in done])
+        qs = np.array([d["queue_s"] for d in done])
+        out.append({"rate_per_s": rate, "requests": len(reqs),
+                    "p50_latency_s": float(np.percentile(lat, 50)),
+                    "p99_latency_s": float(np.percentile(lat, 99)),
+                    "p50_queue_s": float(np.percentile(qs, 50)),
+                    "completed_iterations_per_sec": float(sum(Is) / (t_end - t_start)),
+                    "max_concurrent_requests": maxrun,
+                    "wall_s": t_end - t_start})
+    line = {
+        "metric": "serve_p99_latency_s", "value": out[-1]["p99_latency_s"], "unit": "s",
+        "n_gpus": world, "steps": 1, "warmup": 0, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded Taixxa-like instances, Poisson arrivals)",
+        "config": {"workload": wl["desc"]}, "sweep": out,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -321,6 +462,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch512":
+        run_batch(args, rank, world, local_rank)
+        return
+    if args.workload == "serve":
+        run_serve(args, rank, world, local_rank)
         return
     dist = None
     if world > 1:

@@ -149,18 +149,27 @@ struct qap_sa {
 
 namespace {
 
+// Device memory of a handle is stream-ordered (cudaMallocAsync/cudaFreeAsync on
+// the handle's stream): unlike cudaFree, freeing it never waits for the work
+// of other streams, so chains that run side by side (the server, the batch
+// set-up) never serialise on each other's allocations.
+void dfree(void *p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
 void free_handle(qap_sa *h) {
   if (!h) return;
-  if (h->stream) cudaStreamSynchronize(h->stream);
-  cudaFree(h->A8);
-  cudaFree(h->Bp8);
-  cudaFree(h->delta);
-  cudaFree(h->p);
-  cudaFree(h->d);
-  cudaFree(h->st);
-  cudaFree(h->P);
-  cudaFree(h->tiles);
-  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  cudaStream_t st = h->stream;
+  if (st) cudaStreamSynchronize(st);
+  dfree(h->A8, st);
+  dfree(h->Bp8, st);
+  dfree(h->delta, st);
+  dfree(h->p, st);
+  dfree(h->d, st);
+  dfree(h->st, st);
+  dfree(h->P, st);
+  dfree(h->tiles, st);
+  if (h->own_stream && st) cudaStreamDestroy(st);
   delete h;
 }
 
@@ -266,11 +275,26 @@ cudaError_t launch_tier2(const ChainDev &g, unsigned long long it_end, int C,
   return cudaLaunchKernelEx(&cfg, sa_tier2_kernel, g, it_end);
 }
 
+// Keep freed stream-ordered memory in the device's default pool instead of
+// returning it at every synchronisation (once per device).
+void keep_pool_memory() {
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done[dev] = true;
+}
+
 // Common body of the two create entry points; A32/B32/p032 are device
 // pointers that stay valid for the duration of the call.
 int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
                   const int32_t *p032, const qap_schedule *sc, uint64_t seed,
                   cudaStream_t stream, bool own_stream, qap_sa **out) {
+  keep_pool_memory();
   qap_sa *h = new (std::nothrow) qap_sa();
   if (!h) return QAP_E_NOMEM;
   h->N = N;
@@ -284,9 +308,9 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   SetupOut *so = nullptr;
   SetupOut so_h{};
   auto fail = [&](int code) {
-    cudaFree(count);
-    cudaFree(G);
-    cudaFree(so);
+    dfree(count, stream);
+    dfree(G, stream);
+    dfree(so, stream);
     free_handle(h);
     return code;
   };
@@ -296,21 +320,22 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
     if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call)); \
   } while (0)
   const size_t nS = (size_t)N * S;
-  CKF(cudaMalloc(&h->A8, nS));
-  CKF(cudaMalloc(&h->Bp8, nS));
-  CKF(cudaMalloc(&h->delta, sizeof(int) * (size_t)(M > 0 ? M : 1)));
-  CKF(cudaMalloc(&h->p, sizeof(int) * N));
-  CKF(cudaMalloc(&h->d, sizeof(int) * N));
-  CKF(cudaMalloc(&h->st, sizeof(ChainStatus)));
-  CKF(cudaMalloc(&h->P, sizeof(double) * 8 * 256));
+  CKF(cudaMallocAsync((void **)&h->A8, nS, stream));
+  CKF(cudaMallocAsync((void **)&h->Bp8, nS, stream));
+  CKF(cudaMallocAsync((void **)&h->delta, sizeof(int) * (size_t)(M > 0 ? M : 1), stream));
+  CKF(cudaMallocAsync((void **)&h->p, sizeof(int) * N, stream));
+  CKF(cudaMallocAsync((void **)&h->d, sizeof(int) * N, stream));
+  CKF(cudaMallocAsync((void **)&h->st, sizeof(ChainStatus), stream));
+  CKF(cudaMallocAsync((void **)&h->P, sizeof(double) * 8 * 256, stream));
   h->tier = N <= max_n_tier1() ? 1 : 2;
   const std::vector<int> tiles = make_tiles(N, h->tier == 1 ? tile_rows(N) : kT2R);
-  CKF(cudaMalloc(&h->tiles, sizeof(int) * (tiles.size() ? tiles.size() : 1)));
+  CKF(cudaMallocAsync((void **)&h->tiles, sizeof(int) * (tiles.size() ? tiles.size() : 1),
+                      stream));
   CKF(cudaMemcpyAsync(h->tiles, tiles.data(), sizeof(int) * tiles.size(),
                       cudaMemcpyHostToDevice, stream));
-  CKF(cudaMalloc(&count, sizeof(int) * N));
-  CKF(cudaMalloc(&G, sizeof(int) * (size_t)N * N));
-  CKF(cudaMalloc(&so, sizeof(SetupOut)));
+  CKF(cudaMallocAsync((void **)&count, sizeof(int) * N, stream));
+  CKF(cudaMallocAsync((void **)&G, sizeof(int) * (size_t)N * N, stream));
+  CKF(cudaMallocAsync((void **)&so, sizeof(SetupOut), stream));
   CKF(cudaMemsetAsync(h->A8, 0, nS, stream));
   CKF(cudaMemsetAsync(h->Bp8, 0, nS, stream));
   CKF(cudaMemsetAsync(count, 0, sizeof(int) * N, stream));
@@ -331,11 +356,11 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   }
   CKF(cudaMemcpyAsync(&so_h, so, sizeof so_h, cudaMemcpyDeviceToHost, stream));
   CKF(cudaStreamSynchronize(stream));
-  cudaFree(count);
+  dfree(count, stream);
   count = nullptr;
-  cudaFree(G);
+  dfree(G, stream);
   G = nullptr;
-  cudaFree(so);
+  dfree(so, stream);
   so = nullptr;
   if (so_h.flags & (kFlagAsym | kFlagDiag | kFlagPerm)) return fail(QAP_E_INVAL);
   if (so_h.flags & (kFlagRangeA | kFlagRangeB)) return fail(QAP_E_RANGE);
@@ -450,28 +475,31 @@ int create_from_host(const int32_t *A, const int32_t *B, int32_t N,
   int rc = QAP_OK;
   int32_t *dA = nullptr, *dB = nullptr, *dp = nullptr;
   const size_t nn = sizeof(int32_t) * (size_t)N * N;
-  cudaError_t e = cudaMalloc(&dA, nn);
-  if (e == cudaSuccess) e = cudaMalloc(&dB, nn);
-  if (e == cudaSuccess) e = cudaMalloc(&dp, sizeof(int32_t) * N);
+  cudaError_t e = cudaMallocAsync((void **)&dA, nn, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&dB, nn, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&dp, sizeof(int32_t) * N, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dA, A, nn, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dB, B, nn, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dp, p0, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) {
     rc = cuda_fail(e, "staging copy");
+    dfree(dA, st);
+    dfree(dB, st);
+    dfree(dp, st);
     cudaStreamSynchronize(st);
-    cudaFree(dA);
-    cudaFree(dB);
-    cudaFree(dp);
     if (own_stream) cudaStreamDestroy(st);
     return rc;
   }
   // create_common synchronises the stream before it returns, and on failure
   // destroys an owned stream together with the partial handle.
   rc = create_common(dA, dB, N, dp, sched, seed, st, own_stream, out);
-  cudaFree(dA);
-  cudaFree(dB);
-  cudaFree(dp);
+  // on success create_common has synchronised st; on failure it destroyed an
+  // owned st, whose pending work (these frees included) still completes
+  cudaStream_t fst = (rc == QAP_OK || !own_stream) ? st : (cudaStream_t)0;
+  dfree(dA, fst);
+  dfree(dB, fst);
+  dfree(dp, fst);
   return rc;
 }
 
@@ -532,7 +560,8 @@ int qap_sa_sync(qap_sa *h) {
   if (!h) return QAP_E_INVAL;
   CK(cudaStreamSynchronize(h->stream));
   int err = 0;
-  CK(cudaMemcpy(&err, &h->st->error, sizeof err, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&err, &h->st->error, sizeof err, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   return err ? QAP_E_STATE : QAP_OK;
 }
 

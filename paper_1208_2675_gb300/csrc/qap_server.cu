@@ -194,6 +194,22 @@ int qap_server_start(const qap_server_cfg *cfg, qap_server **out) {
   s->max_sms = (s->cfg.max_sms > 0 && s->cfg.max_sms < sms) ? s->cfg.max_sms : sms;
   s->budget = s->cfg.mem_budget_bytes ? (size_t)s->cfg.mem_budget_bytes
                                       : (size_t)(0.8 * (double)free_b);
+  // Grow the device's default pool once, now, while nothing runs: growing it
+  // later, with chains on the device, would synchronise with them.  The
+  // library keeps freed pool memory (release threshold raised at set-up).
+  {
+    qap_sa_max_n();  // device attributes and pool settings initialised
+    const size_t reserve = s->budget < ((size_t)4 << 30) ? s->budget : ((size_t)4 << 30);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      void *p = nullptr;
+      if (cudaMallocAsync(&p, reserve, 0) == cudaSuccess) cudaFreeAsync(p, 0);
+      cudaStreamSynchronize(0);
+    }
+    cudaGetLastError();
+  }
   s->worker = std::thread(worker_main, s);
   *out = s;
   return QAP_OK;
