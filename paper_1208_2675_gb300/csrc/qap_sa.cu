@@ -65,12 +65,8 @@ int row_stride(int N) {
   return 16 * c;
 }
 
-// Height of the register tiles of Delta for a problem of size N.
-int tile_rows(int N) { return N <= 128 ? 4 : (N <= 192 ? 8 : 16); }
-
-int tile_bound(int R) {
-  return R == 4 ? T1Bound<4>::threads : (R == 8 ? T1Bound<8>::threads : T1Bound<16>::threads);
-}
+// Height of the register tiles of Delta.
+int tile_rows(int) { return kT1R; }
 
 // R x 4 tiles of the upper triangle that hold at least one pair u < v < N,
 // row-block major, each encoded as first_row << 16 | first_column.
@@ -173,20 +169,18 @@ void free_handle(qap_sa *h) {
   delete h;
 }
 
-// Threads of the tier-1 CTA: one per tile at least, and the whole register
-// budget of the kernel otherwise (more threads shorten the dependent chains of
-// the row recompute and the threshold preparation).
+// Threads of the tier-1 CTA: one per tile and one per row at least, 256 at
+// least; the kernel is compiled for up to 256 and for up to 640 threads.
 int tier1_threads(int N, int ntiles) {
   int nt = ntiles > N ? ntiles : N;
-  const int bound = tile_bound(tile_rows(N));
-  if (nt < bound) nt = bound;
+  if (nt < 256) nt = 256;
   return (nt + 31) & ~31;
 }
 
 int tier1_fits(int N) {
   const int R = tile_rows(N);
   const int nt = tier1_threads(N, (int)make_tiles(N, R).size());
-  if (nt > tile_bound(R)) return 0;
+  if (nt > kT1LargeThreads) return 0;
   return t1_layout(N, row_stride(N)).bytes <= device_smem_optin();
 }
 
@@ -386,6 +380,7 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   {
     ChainStatus st0{};
     st0.cost = so_h.cost0;
+    st0.mode = 1;  // start evaluating proposals directly (hot start)
     CKF(cudaMemcpyAsync(h->st, &st0, sizeof st0, cudaMemcpyHostToDevice,
                         stream));
   }
@@ -423,19 +418,23 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   // Pre-test margin: covers binary32 rounding of T and -ln u, the byte-table
   // product's drift from T0 alpha^it, and the exponent's rounding.
   g.mrel = (float)(2e-5 + 2e-7 * fabs(l2r) + 8.0 * (double)sc->total_iters * 0x1p-53);
+  // Acceptance rate below which the one-SM tier maintains Delta (above it,
+  // proposals are evaluated directly): where one accepted swap's O(N^2) update
+  // costs as much as evaluating ~2000 proposals directly.
+  {
+    const char *e = getenv("QAPSA_HYBRID_RATE");
+    g.hyb_lo = (h->tier == 1) ? (e ? (float)atof(e) : 5e-4f) : 0.0f;
+  }
   h->layout = t1_layout(N, S);
   h->smem_bytes = h->tier == 1 ? h->layout.bytes : t2_layout(N).bytes;
   if (h->tier == 2)
     CKF(cudaFuncSetAttribute(sa_tier2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              h->smem_bytes));
-  else if (h->R == 4)
-    CKF(cudaFuncSetAttribute(sa_tier1_kernel<4>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, h->layout.bytes));
-  else if (h->R == 8)
-    CKF(cudaFuncSetAttribute(sa_tier1_kernel<8>,
+  else if (h->nthreads <= kT1SmallThreads)
+    CKF(cudaFuncSetAttribute(sa_tier1_kernel<kT1SmallThreads>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, h->layout.bytes));
   else
-    CKF(cudaFuncSetAttribute(sa_tier1_kernel<16>,
+    CKF(cudaFuncSetAttribute(sa_tier1_kernel<kT1LargeThreads>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, h->layout.bytes));
   CKF(cudaStreamSynchronize(stream));
   *out = h;
@@ -542,12 +541,13 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
     if (h->tier == 2) {
       cudaError_t e2 = launch_tier2(h->dev, stop, h->cluster, h->smem_bytes, h->stream);
       if (e2 != cudaSuccess) return cuda_fail(e2, "sa_tier2_kernel launch");
-    } else if (h->R == 4)
-      sa_tier1_kernel<4><<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
-    else if (h->R == 8)
-      sa_tier1_kernel<8><<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
-    else
-      sa_tier1_kernel<16><<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
+    } else if (h->nthreads <= kT1SmallThreads) {
+      sa_tier1_kernel<kT1SmallThreads>
+          <<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
+    } else {
+      sa_tier1_kernel<kT1LargeThreads>
+          <<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "sa_tier1_kernel launch");
     cur = stop;

@@ -29,7 +29,7 @@ struct ChainStatus {
   unsigned long long exact_evals; // acceptance tests decided in binary64
   unsigned long long windows;     // windows scanned
   int error;                      // nonzero: device-detected inconsistency
-  int pad;
+  int mode;                       // 1: proposals evaluated directly, 0: from Delta
 };
 
 // Everything one chain's kernels need (passed by value).
@@ -53,6 +53,7 @@ struct ChainDev {
   float T0f;         // binary32 copies for the approximate pre-test
   float log2a_f;     // log2(alpha)
   float mrel;        // relative margin of the approximate pre-test
+  float hyb_lo;      // acceptance rate below which Delta is maintained (0: always)
 };
 
 // ------------------------------------------------------------------------- //

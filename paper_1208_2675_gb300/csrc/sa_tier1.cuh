@@ -59,16 +59,17 @@ __host__ __device__ inline T1Layout t1_layout(int N, int S) {
   return L;
 }
 
-// Threads per CTA the kernel for tile height R is compiled for (register
-// budget: 65536 / bound per thread).
-template <int R> struct T1Bound;
-template <> struct T1Bound<4> { static constexpr int threads = 640; };
-template <> struct T1Bound<8> { static constexpr int threads = 640; };
-template <> struct T1Bound<16> { static constexpr int threads = 640; };
+// Tile height of the register tiles of Delta, and the two thread counts the
+// one-CTA kernel is compiled for: 256 (up to 255 registers per thread) for
+// problems whose tiles fit, 640 (96 registers) above.
+constexpr int kT1R = 16;
+constexpr int kT1SmallThreads = 256;
+constexpr int kT1LargeThreads = 640;
 
-// s_ctl words: three window keys, the d_r / d_s sums, the binary64 verdict,
-// then (from word 8, 8-byte aligned) thread 0's 64-bit counters.
-enum : int { kT1Key0 = 0, kT1Dr = 3, kT1Ds = 4, kT1Dec = 5 };
+// s_ctl words: three window keys, the d_r / d_s sums of even accepts, the
+// binary64 verdict, the d_r / d_s sums of odd accepts, then (from word 8,
+// 8-byte aligned) thread 0's 64-bit counters.
+enum : int { kT1Key0 = 0, kT1Dr = 3, kT1Ds = 4, kT1Dec = 5, kT1Dr1 = 6, kT1Ds1 = 7 };
 enum : int { kC64Accepts = 0, kC64Cost = 1, kC64Near = 2, kC64Exact = 3, kC64Windows = 4 };
 
 __device__ __forceinline__ float u64_to_f32(unsigned long long x) {
@@ -79,6 +80,25 @@ __device__ __forceinline__ float u64_to_f32(unsigned long long x) {
 // Pair index of (u, v), u < v, in the row-major enumeration of pairs r < s.
 __device__ __forceinline__ int pidx(int N, int u, int v) {
   return u * N - (u * (u + 1)) / 2 + (v - u - 1);
+}
+
+// (r, s) = pair number m of the row-major enumeration of pairs r < s.
+__device__ __forceinline__ void decode_pair(int N, int m, int &r, int &s) {
+  const float f2n = (float)(2 * N - 1);
+  int q = (int)((f2n - sqrtf(fmaxf(f2n * f2n - 8.0f * (float)m, 0.0f))) * 0.5f);
+  q = max(0, min(q, N - 2));
+  while (q > 0 && q * N - (q * (q + 1)) / 2 > m) --q;
+  while (q < N - 2 && (q + 1) * N - ((q + 1) * (q + 2)) / 2 <= m) ++q;
+  r = q;
+  s = m - (q * N - (q * (q + 1)) / 2) + q + 1;
+}
+
+// The pair after (r, s) in the cyclic enumeration.
+__device__ __forceinline__ void next_pair(int N, int &r, int &s) {
+  if (++s >= N) {
+    if (++r >= N - 1) r = 0;
+    s = r + 1;
+  }
 }
 
 // Does the closed interval [lo, hi] of pair indices meet the window, which
@@ -134,8 +154,49 @@ __device__ __noinline__ unsigned pretest_cells(unsigned long long seed,
   return out;
 }
 
+// Delta of the cells of one tile from their definition under the current p,
+// through G_xy = <A_x, B'_y>: Delta_uv = 2 (G_uv + G_vu - d_u - d_v + 2 A_uv B'_uv).
+template <int R>
+__device__ __forceinline__ void t1_rebuild_tile(int (&D)[R][4], int u0, int v0,
+                                                int N, int S, const int8_t *s_A,
+                                                const int8_t *s_B, const int *s_d) {
+  const int NC = S >> 4;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int u = u0 + i, v = v0 + c;
+      if (!(u < v && v < N)) continue;
+      const int4 *Au = reinterpret_cast<const int4 *>(s_A + u * S);
+      const int4 *Bu = reinterpret_cast<const int4 *>(s_B + u * S);
+      const int4 *Av = reinterpret_cast<const int4 *>(s_A + v * S);
+      const int4 *Bv = reinterpret_cast<const int4 *>(s_B + v * S);
+      int guv = 0, gvu = 0;
+      for (int k = 0; k < NC; ++k) {
+        const int4 a = Au[k], b = Bv[k], a2 = Av[k], b2 = Bu[k];
+        guv = __dp4a(a.x, b.x, guv); guv = __dp4a(a.y, b.y, guv);
+        guv = __dp4a(a.z, b.z, guv); guv = __dp4a(a.w, b.w, guv);
+        gvu = __dp4a(a2.x, b2.x, gvu); gvu = __dp4a(a2.y, b2.y, gvu);
+        gvu = __dp4a(a2.z, b2.z, gvu); gvu = __dp4a(a2.w, b2.w, gvu);
+      }
+      D[i][c] = 2 * (guv + gvu - s_d[u] - s_d[v] + 2 * (int)s_A[u * S + v] * (int)s_B[u * S + v]);
+    }
+}
+
 // One chain, run by the whole CTA from its state in global memory to iteration
 // it_end and written back.  `smem` holds at least t1_layout(N, S).bytes.
+//
+// Two ways to obtain the swap cost of a proposal, chosen by the measured
+// acceptance rate (the trajectory is the same either way: delta is the same
+// exact integer):
+//   Delta mode   the maintained matrix (section 2.2): a proposal costs one
+//                register read, an accepted swap the O(N^2) update;
+//   direct mode  delta = 2 (<A_r, B'_s> + <A_s, B'_r> - d_r - d_s + 2 A_rs B'_rs)
+//                evaluated for every proposal of the window (four threads per
+//                proposal, dp4a), and an accepted swap only moves p, B' and d.
+// While many proposals are accepted (high temperature) direct mode is far
+// cheaper; the kernel switches to Delta mode, rebuilding Delta, once the
+// acceptance rate of a block of 16384 iterations drops below g.hyb_lo.
 template <int R>
 __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
                                              unsigned long long it_end,
@@ -211,12 +272,26 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
   unsigned long long it = g.st->it;
   int err = 0;
   int mb = (int)(it % (unsigned long long)M);  // pair index of iteration it
+  int cr, cs;                                   // that pair, (cr, cs)
+  decode_pair(N, mb, cr, cs);
   int K = min(1024, M);                         // window length
+  (void)K;
   unsigned wi = 0;
   int pend_r = -1, pend_s = -1;
   unsigned long long tab_it = 0;  // first iteration covered by s_tt
   int tab_len = 0;                // entries of s_tt that are valid
-  const int tpv = g.tpv, lpt = 32 / tpv;  // lanes per dot-product slice
+  int mode = (g.hyb_lo > 0.0f) ? g.st->mode : 0;
+  int blk_it = 0, blk_acc = 0;    // iterations and accepts of the current block
+  bool rebuild = false;           // Delta registers to be recomputed
+  // Direct mode: d of the last swap's r and s, taken from the reduction while
+  // s_d[r], s_d[s] are being written (one barrier fewer per accepted swap).
+  int ov_r = -1, ov_s = -1, ov_dr = 0, ov_ds = 0;
+  unsigned nacc = 0;  // accepted swaps in this launch: d_r, d_s sums alternate
+  const int per_pass = nthreads >> 2;  // proposals evaluated at once, direct mode
+  int tpv = 1;  // threads per row in the rows-r,s recompute: <= 4 keeps >= 8
+                // lanes per slice, so 16-byte loads of 8 rows are conflict-free
+  while (tpv < 4 && 2 * tpv * N <= nthreads) tpv *= 2;
+  const int lpt = 32 / tpv;  // lanes per dot-product slice
   const int t_sl = lane / lpt, v_l = lane - t_sl * lpt;
   const int vslots = (nthreads >> 5) * lpt;
   const int NC = S >> 4;  // 16-byte chunks per row
@@ -250,7 +325,13 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
       }
     }
     pend_r = -1;
-    if (it >= it_end || err) break;
+    // Delta registers from their definition: after a switch to Delta mode, and
+    // before the state is stored if Delta was not being maintained.
+    const bool last = it >= it_end || err;
+    if (has_tile && (rebuild || (last && mode == 1)))
+      t1_rebuild_tile<R>(D, u0, v0, N, S, s_A, s_B, s_d);
+    rebuild = false;
+    if (last) break;
 
     // ================= scan one window =================
     // Window = iterations it .. it + wlen - 1, wlen <= M, so the proposal at
@@ -272,7 +353,67 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
     }
     unsigned best = kNone;
     int bu = 0, bv = 0, bd = 0;
-    if (has_tile && meets_window(tm_lo, tm_hi, mb, wlen, M)) {
+    if (mode == 1) {
+      // ---- direct evaluation: four threads per proposal ----
+      const int sub = tid & 3;
+      for (int jb = 0; jb < wlen; jb += per_pass) {
+        const int j = jb + (tid >> 2);
+        int r = cr, s = cs + j, g1 = 0, g2 = 0;
+        if (j < wlen) {
+          if (s >= N) {  // beyond the window's first row
+            int m = mb + j;
+            if (m >= M) m -= M;
+            decode_pair(N, m, r, s);
+          }
+          const int4 *Ar4 = reinterpret_cast<const int4 *>(s_A + r * S);
+          const int4 *As4 = reinterpret_cast<const int4 *>(s_A + s * S);
+          const int4 *Br4 = reinterpret_cast<const int4 *>(s_B + r * S);
+          const int4 *Bs4 = reinterpret_cast<const int4 *>(s_B + s * S);
+          for (int c = sub; c < NC; c += 4) {
+            const int4 a = Ar4[c], b = Bs4[c];
+            g1 = __dp4a(a.x, b.x, g1); g1 = __dp4a(a.y, b.y, g1);
+            g1 = __dp4a(a.z, b.z, g1); g1 = __dp4a(a.w, b.w, g1);
+            const int4 a2 = As4[c], b2 = Br4[c];
+            g2 = __dp4a(a2.x, b2.x, g2); g2 = __dp4a(a2.y, b2.y, g2);
+            g2 = __dp4a(a2.z, b2.z, g2); g2 = __dp4a(a2.w, b2.w, g2);
+          }
+        }
+        g1 += __shfl_xor_sync(0xFFFFFFFFu, g1, 1);
+        g2 += __shfl_xor_sync(0xFFFFFFFFu, g2, 1);
+        g1 += __shfl_xor_sync(0xFFFFFFFFu, g1, 2);
+        g2 += __shfl_xor_sync(0xFFFFFFFFu, g2, 2);
+        if (sub == 0 && j < wlen) {
+          const int dr_ = (r == ov_r) ? ov_dr : (r == ov_s ? ov_ds : s_d[r]);
+          const int ds_ = (s == ov_r) ? ov_dr : (s == ov_s ? ov_ds : s_d[s]);
+          const int dv = 2 * (g1 + g2 - dr_ - ds_ +
+                              2 * (int)s_A[r * S + s] * (int)s_B[r * S + s]);
+          unsigned acc = 0, unc = 0;
+          const int jt = jt0 + j;
+          if (dv <= 0) {
+            acc = 1;
+          } else if (jt < tab_len) {
+            const float2 b = s_tt[jt];
+            const float df = (float)dv;
+            if (df < b.x) acc = 1;
+            else if (!(df > b.y)) unc = 1;
+          } else if (dv <= thr) {
+            const unsigned o = pretest_cells(g.seed, g.stream, g.log2a_f, g.mrel, it, Tw,
+                                             j, 0, 0, 0, dv, 0, 0, 0, 1u);
+            acc = o & 1u;
+            unc = (o >> 4) & 1u;
+          }
+          if (acc | unc) {
+            const unsigned key = ((unsigned)j << 1) | unc;
+            if (key < best) {
+              best = key;
+              bu = r;
+              bv = s;
+              bd = dv;
+            }
+          }
+        }
+      }
+    } else if (has_tile && meets_window(tm_lo, tm_hi, mb, wlen, M)) {
 #pragma unroll
       for (int i = 0; i < R; ++i) {
         const int u = u0 + i;
@@ -337,13 +478,23 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
       s_ctl[kT1Key0 + ((wi + 2u) % 3u)] = kNone;
       ++c64[kC64Windows];
     }
+    ov_r = ov_s = -1;  // s_d[r], s_d[s] are current after this barrier
     ++wi;
 
     if (code == kNone) {  // nothing accepted in the window
       mb += wlen;
       if (mb >= M) mb -= M;
+      decode_pair(N, mb, cr, cs);
       it += (unsigned)wlen;
-      K = min(K * 2, M);
+      K = min(K * 2, mode == 1 ? min(M, 4 * per_pass) : M);
+      blk_it += wlen;
+      if (blk_it >= 16384) {
+        if (mode == 1 && (float)blk_acc < g.hyb_lo * (float)blk_it) {
+          mode = 0;  // few accepts: maintain Delta from here on
+          rebuild = true;
+        }
+        blk_it = blk_acc = 0;
+      }
       continue;
     }
     const int j = (int)(code >> 6);
@@ -361,6 +512,9 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
         it += (unsigned)j + 1;
         mb += j + 1;
         if (mb >= M) mb -= M;
+        cr = r;
+        cs = s;
+        next_pair(N, cr, cs);
         continue;
       }
     }
@@ -371,10 +525,15 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
       continue;
     }
     if (j < K / 8) K = max(64, K / 2);
-    K = min(K, M);
+    K = min(K, mode == 1 ? min(M, 4 * per_pass) : M);
+    blk_it += j + 1;
+    ++blk_acc;
     it += (unsigned)j + 1;
     mb += j + 1;
     if (mb >= M) mb -= M;
+    cr = r;
+    cs = s;
+    next_pair(N, cr, cs);
     if (tid == 0) {
       ++c64[kC64Accepts];
       c64[kC64Cost] += (unsigned long long)(long long)dlt;
@@ -412,15 +571,17 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
       dr_part = __reduce_add_sync(0xFFFFFFFFu, dr_part);
       ds_part = __reduce_add_sync(0xFFFFFFFFu, ds_part);
       if (lane == 0) {
-        atomicAdd(reinterpret_cast<int *>(s_ctl + kT1Dr), dr_part);
-        atomicAdd(reinterpret_cast<int *>(s_ctl + kT1Ds), ds_part);
+        atomicAdd(reinterpret_cast<int *>(s_ctl + ((nacc & 1u) ? kT1Dr1 : kT1Dr)), dr_part);
+        atomicAdd(reinterpret_cast<int *>(s_ctl + ((nacc & 1u) ? kT1Ds1 : kT1Ds)), ds_part);
       }
     }
-    __syncthreads();
-    const int dr = (int)s_ctl[kT1Dr], ds = (int)s_ctl[kT1Ds];
-
+    if (tid == 0) {  // the other pair: last read before the previous window's
+                     // barrier, next written after this stage's barrier
+      s_ctl[(nacc & 1u) ? kT1Dr : kT1Dr1] = 0u;
+      s_ctl[(nacc & 1u) ? kT1Ds : kT1Ds1] = 0u;
+    }
     // ---- thresholds of the next window [it, it + tab_len), one Philox
-    //      block per thread ----
+    //      block per thread, on the last warps (free during the stage) ----
     tab_it = it;
     tab_len = min(K, kTabMax);
     {
@@ -442,6 +603,12 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
       }
     }
 
+    __syncthreads();
+    const int dr = (int)s_ctl[(nacc & 1u) ? kT1Dr1 : kT1Dr];
+    const int ds = (int)s_ctl[(nacc & 1u) ? kT1Ds1 : kT1Ds];
+    ++nacc;
+
+    if (mode == 0) {
     // ---- rows r,s under the new p through G_xy = <A_x, B'_y>:
     //      Delta_rv = 2 (G_rv + G_vr - d_r - d_v + 2 A_rv B'_rv) ----
     {
@@ -502,19 +669,39 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
         D[i][3] += (au - av.w) * (bv.w - bu_);
       }
     }
-    if (tid == 0) {
-      s_nr[s] = -dlt;
-      s_ns[r] = -dlt;
-      s_d[r] = dr;
-      s_d[s] = ds;
     }
-    __syncthreads();
-    if (tid == 0) {
-      s_ctl[kT1Dr] = 0u;
-      s_ctl[kT1Ds] = 0u;
+    if (mode == 0) {
+      if (tid == 0) {
+        s_nr[s] = -dlt;
+        s_ns[r] = -dlt;
+        s_d[r] = dr;
+        s_d[s] = ds;
+      }
+      __syncthreads();
+      pend_r = r;
+      pend_s = s;
+    } else {
+      // no barrier: the next window reads d_r, d_s from these registers while
+      // thread 0 stores them; the accumulators are cleared after its barrier
+      ov_r = r;
+      ov_s = s;
+      ov_dr = dr;
+      ov_ds = ds;
+      if (tid == 0) {
+        s_d[r] = dr;
+        s_d[s] = ds;
+      }
     }
-    pend_r = r;
-    pend_s = s;
+    if (blk_it >= 16384) {
+      if (mode == 1 && (float)blk_acc < g.hyb_lo * (float)blk_it) {
+        mode = 0;  // few accepts: maintain Delta from here on
+        rebuild = true;
+      } else if (mode == 0 && g.hyb_lo > 0.0f &&
+                 (float)blk_acc > 4.0f * g.hyb_lo * (float)blk_it) {
+        mode = 1;  // many accepts again: evaluate proposals directly
+      }
+      blk_it = blk_acc = 0;
+    }
   }
 
   // ---- state back to global memory ----
@@ -542,15 +729,16 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
     g.st->near_ties += c64[kC64Near];
     g.st->exact_evals += c64[kC64Exact];
     g.st->windows += c64[kC64Windows];
+    g.st->mode = mode;
     if (err) g.st->error = err;
   }
 }
 
-template <int R>
-__global__ void __launch_bounds__(T1Bound<R>::threads, 1)
+template <int BOUND>
+__global__ void __launch_bounds__(BOUND, 1)
     sa_tier1_kernel(ChainDev g, unsigned long long it_end) {
   extern __shared__ __align__(16) unsigned char smem[];
-  t1_run_chain<R>(g, it_end, smem);
+  t1_run_chain<kT1R>(g, it_end, smem);
 }
 
 // ------------------------------------------------------------------------- //
@@ -581,9 +769,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     const int k = s_next;
     if (k >= n) return;
     const BatchChain &bc = chains[order[k]];
-    if (bc.R == 4) t1_run_chain<4>(bc.g, bc.it_end, smem);
-    else if (bc.R == 8) t1_run_chain<8>(bc.g, bc.it_end, smem);
-    else t1_run_chain<16>(bc.g, bc.it_end, smem);
+    t1_run_chain<kT1R>(bc.g, bc.it_end, smem);
   }
 }
 

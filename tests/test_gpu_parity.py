@@ -260,3 +260,16 @@ def test_n1024_grid_workload_prefix_matches_oracle():
     assert g.info()["tier"] == 2
     assert os_["accepts"] > 300
     assert_same(gs, os_, gd, od)
+
+
+@pytest.mark.parametrize("rate", ["0", "1e-9", "5e-4", "1.0"])
+def test_direct_and_delta_modes_give_the_same_trajectory(rate, monkeypatch):
+    """Proposals evaluated directly or read from the maintained Delta: the same
+    exact integer either way.  rate = 0: Delta throughout; 1e-9: direct
+    throughout; 5e-4: the default switch point; 1.0: switch after the first block."""
+    monkeypatch.setenv("QAPSA_HYBRID_RATE", rate)
+    A, B, p0 = instances.taixxa_like(64, 41)
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=400000, seed=41,
+                                     splits=[150000, 250000])
+    assert os_["accepts"] > 1000
+    assert_same(gs, os_, gd, od)
