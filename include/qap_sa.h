@@ -142,6 +142,9 @@ typedef struct qap_sa_info {
   double T0, Tf, alpha;   /* the schedule actually used                     */
   uint64_t total_iters;
   uint64_t smem_bytes;    /* dynamic shared memory of the SA kernel         */
+  uint64_t direct_iters;  /* iterations whose proposal was evaluated directly
+                             (high acceptance) instead of read from Delta  */
+  uint64_t direct_accepts;/* accepted swaps among them (no Delta update)    */
 } qap_sa_info;
 QAP_EXPORT int qap_sa_get_info(qap_sa *h, qap_sa_info *out);
 

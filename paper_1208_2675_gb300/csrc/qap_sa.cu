@@ -620,6 +620,8 @@ int qap_sa_get_info(qap_sa *h, qap_sa_info *out) {
   out->alpha = h->sched.alpha;
   out->total_iters = h->sched.I;
   out->smem_bytes = (uint64_t)h->smem_bytes;
+  out->direct_iters = st.direct_iters;
+  out->direct_accepts = st.direct_accepts;
   return st.error ? QAP_E_STATE : QAP_OK;
 }
 

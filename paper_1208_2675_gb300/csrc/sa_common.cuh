@@ -30,6 +30,8 @@ struct ChainStatus {
   unsigned long long windows;     // windows scanned
   int error;                      // nonzero: device-detected inconsistency
   int mode;                       // 1: proposals evaluated directly, 0: from Delta
+  unsigned long long direct_iters;    // iterations whose proposal was evaluated directly
+  unsigned long long direct_accepts;  // accepted swaps among them
 };
 
 // Everything one chain's kernels need (passed by value).

@@ -70,7 +70,8 @@ constexpr int kT1LargeThreads = 640;
 // binary64 verdict, the d_r / d_s sums of odd accepts, then (from word 8,
 // 8-byte aligned) thread 0's 64-bit counters.
 enum : int { kT1Key0 = 0, kT1Dr = 3, kT1Ds = 4, kT1Dec = 5, kT1Dr1 = 6, kT1Ds1 = 7 };
-enum : int { kC64Accepts = 0, kC64Cost = 1, kC64Near = 2, kC64Exact = 3, kC64Windows = 4 };
+enum : int { kC64Accepts = 0, kC64Cost = 1, kC64Near = 2, kC64Exact = 3, kC64Windows = 4,
+              kC64DirIt = 5, kC64DirAcc = 6 };
 
 __device__ __forceinline__ float u64_to_f32(unsigned long long x) {
   return __uint2float_rn((unsigned)(x >> 32)) * 4294967296.0f +
@@ -268,6 +269,8 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
     c64[kC64Near] = 0;
     c64[kC64Exact] = 0;
     c64[kC64Windows] = 0;
+    c64[kC64DirIt] = 0;
+    c64[kC64DirAcc] = 0;
   }
   unsigned long long it = g.st->it;
   int err = 0;
@@ -485,6 +488,7 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
       mb += wlen;
       if (mb >= M) mb -= M;
       decode_pair(N, mb, cr, cs);
+      if (tid == 0 && mode == 1) c64[kC64DirIt] += (unsigned)wlen;
       it += (unsigned)wlen;
       K = min(K * 2, mode == 1 ? min(M, 4 * per_pass) : M);
       blk_it += wlen;
@@ -509,6 +513,7 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
       }
       __syncthreads();
       if (!s_ctl[kT1Dec]) {
+        if (tid == 0 && mode == 1) c64[kC64DirIt] += (unsigned)j + 1;
         it += (unsigned)j + 1;
         mb += j + 1;
         if (mb >= M) mb -= M;
@@ -528,6 +533,10 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
     K = min(K, mode == 1 ? min(M, 4 * per_pass) : M);
     blk_it += j + 1;
     ++blk_acc;
+    if (tid == 0 && mode == 1) {
+      c64[kC64DirIt] += (unsigned)j + 1;
+      ++c64[kC64DirAcc];
+    }
     it += (unsigned)j + 1;
     mb += j + 1;
     if (mb >= M) mb -= M;
@@ -729,6 +738,8 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
     g.st->near_ties += c64[kC64Near];
     g.st->exact_evals += c64[kC64Exact];
     g.st->windows += c64[kC64Windows];
+    g.st->direct_iters += c64[kC64DirIt];
+    g.st->direct_accepts += c64[kC64DirAcc];
     g.st->mode = mode;
     if (err) g.st->error = err;
   }

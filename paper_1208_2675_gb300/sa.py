@@ -42,7 +42,8 @@ class qap_sa_info(ctypes.Structure):
                 ("exact_evals", ctypes.c_uint64), ("windows", ctypes.c_uint64),
                 ("T0", ctypes.c_double), ("Tf", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("total_iters", ctypes.c_uint64),
-                ("smem_bytes", ctypes.c_uint64)]
+                ("smem_bytes", ctypes.c_uint64), ("direct_iters", ctypes.c_uint64),
+                ("direct_accepts", ctypes.c_uint64)]
 
 
 class qap_problem(ctypes.Structure):
