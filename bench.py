@@ -148,9 +148,8 @@ class Clocks:
 # our arm
 # --------------------------------------------------------------------------- #
 def run_ours(args, rank: int, world: int, local_rank: int, dist):
-    import numpy as np
     import torch
-    from paper_1208_2675_gb300 import instances, sa
+    from paper_1208_2675_gb300 import instances, replicas, sa
 
     wl = WORKLOADS[args.workload]
     N, I, seed = wl["N"], wl["I"], wl["seed"]
@@ -166,7 +165,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         cpu_proc, cpu_q = oracle_sample_seconds(N, I_sample, seed)
 
     A, B, p0 = instances.taixxa_like(N, seed)
-    stream_id = rank  # independent replicas: own Philox stream per rank
+    stream_id = replicas.stream_id_for(rank)  # independent replicas
     kw = dict(t0=0.5, tf=1e-3, total_iters=I, seed=seed, stream_id=stream_id)
     At, Bt, pt = (torch.from_numpy(x).to(dev) for x in (A, B, p0))
     p_out = torch.zeros(N, dtype=torch.int32, device=dev)
@@ -214,12 +213,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total = sum(t_steps)
-    if dist:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_max = float(t.item())
-    else:
-        total_max = total
+    total_max = replicas.max_over_ranks(total, dist, dev)
 
     # ---- end to end through the host-pointer API (pinned host buffers) ----
     Ah = torch.from_numpy(A).pin_memory()
@@ -354,14 +348,18 @@ def _batch_problems(wl):
     return probs
 
 
-def run_batch(args, rank, world, local_rank):
+def run_batch(args, rank, world, local_rank, dist):
     import torch
-    from paper_1208_2675_gb300 import sa
+    from paper_1208_2675_gb300 import replicas, sa
     wl = WORKLOADS["batch512"]
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
-    probs = _batch_problems(wl)
+    all_probs = _batch_problems(wl)
     I = wl["I"]
+    # replicas: this rank's share of the chains, balanced by estimated work
+    parts = replicas.partition_by_cost(
+        [replicas.chain_cost(len(pr["p0"]), I) for pr in all_probs], world)
+    probs = [all_probs[i] for i in parts[rank]]
 
     def step():
         t0 = time.perf_counter()
@@ -375,12 +373,14 @@ def run_batch(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         step()
+    if dist:
+        dist.barrier()
     clocks = Clocks(local_rank)
     clocks.start()
     res = [step() for _ in range(args.steps)]
     clk = clocks.stop()
-    t_step = statistics.mean(r[0] for r in res)
-    t_run = statistics.mean(r[1] for r in res)
+    t_step = replicas.max_over_ranks(statistics.mean(r[0] for r in res), dist, dev)
+    t_run = replicas.max_over_ranks(statistics.mean(r[1] for r in res), dist, dev)
     # the plain single-chain path on the same GPU: chains one after another
     single = []
     for pr in probs[:6]:
@@ -390,10 +390,10 @@ def run_batch(args, rank, world, local_rank):
         h.run(I)
         single.append((time.perf_counter() - t, len(pr["p0"])))
         h.close()
-    n = len(probs)
+    n = len(all_probs)
     per_chain = statistics.mean(t for t, _ in single)
     line = {
-        "metric": "batched_chains_per_sec", "value": world * n / t_step, "unit": "chains/s",
+        "metric": "batched_chains_per_sec", "value": n / t_step, "unit": "chains/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded Taixxa-like instances)",
@@ -401,7 +401,7 @@ def run_batch(args, rank, world, local_rank):
                    "sizes": "N ~ U{20..300}", "parallelism": f"replicas x{world}"},
         "run_only_chains_per_sec": n / t_run,
         "iterations_per_sec": n * I / t_step,
-        "accept_rate": statistics.mean(r[2] for r in res) / (n * I),
+        "accept_rate": statistics.mean(r[2] for r in res) / (len(probs) * I),
         "single_chain_path": {"chains_per_sec": 1.0 / per_chain,
                               "sample": f"first {len(single)} chains run one after another "
                                         f"with qap_sa_run (N = {[m for _, m in single]})"},
@@ -415,6 +415,8 @@ def run_batch(args, rank, world, local_rank):
 # serving: Poisson request streams through the continuous-batching server
 # --------------------------------------------------------------------------- #
 def run_serve(args, rank, world, local_rank):
+    if rank != 0:  # the serving sample runs on one GPU
+        return
     import numpy as np
     import torch
     from paper_1208_2675_gb300 import instances, sa
@@ -476,12 +478,6 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.workload == "batch512":
-        run_batch(args, rank, world, local_rank)
-        return
-    if args.workload == "serve":
-        run_serve(args, rank, world, local_rank)
-        return
     dist = None
     if world > 1:
         import torch
@@ -489,7 +485,12 @@ def main():
         torch.cuda.set_device(local_rank)
         tdist.init_process_group("nccl")
         dist = tdist
-    run_ours(args, rank, world, local_rank, dist)
+    if args.workload == "batch512":
+        run_batch(args, rank, world, local_rank, dist)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank, dist)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
