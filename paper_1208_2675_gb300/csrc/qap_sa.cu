@@ -240,9 +240,31 @@ int tier2_fits(int N) {
   return ok_for[C] > 0;
 }
 
+// Load every kernel of the library now (once per process).  With lazy module
+// loading the first launch of a kernel loads its code, and that waits for work
+// already running on the device -- a request served on the cluster tier while
+// one-SM chains run would stall until they finish.
+void preload_kernels() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncAttributes a;
+    cudaFuncGetAttributes(&a, setup_pack_kernel);
+    cudaFuncGetAttributes(&a, setup_bprime_kernel);
+    cudaFuncGetAttributes(&a, setup_gram_kernel);
+    cudaFuncGetAttributes(&a, setup_delta_kernel);
+    cudaFuncGetAttributes(&a, sa_tier1_kernel<kT1SmallThreads>);
+    cudaFuncGetAttributes(&a, sa_tier1_kernel<kT1LargeThreads>);
+    cudaFuncGetAttributes(&a, sa_tier2_kernel);
+    cudaFuncGetAttributes(&a, sa_batch_kernel);
+    cudaFuncGetAttributes(&a, sa_tier2_batch_kernel);
+    cudaGetLastError();
+  });
+}
+
 int max_n_any() {
   static int cached = -1;
   if (cached >= 0) return cached;
+  preload_kernels();
   int best = max_n_tier1();
   for (int N = best + 1; N <= 2048; ++N) {
     if (tier2_cluster(N) > kT2MaxCluster) break;
@@ -288,6 +310,7 @@ void keep_pool_memory() {
 int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
                   const int32_t *p032, const qap_schedule *sc, uint64_t seed,
                   cudaStream_t stream, bool own_stream, qap_sa **out) {
+  preload_kernels();
   keep_pool_memory();
   qap_sa *h = new (std::nothrow) qap_sa();
   if (!h) return QAP_E_NOMEM;
