@@ -198,29 +198,57 @@ int max_n_tier1() {
 }
 
 // Tier 2: one chain on a cluster of C CTAs of 640 threads, R = 16 tiles.
+// Load every kernel of the library now (once per process) and give each the
+// device's whole opt-in shared memory as its limit, so that handles of
+// different N never lower the limit under one another's launches.  With lazy
+// module loading the first launch of a kernel loads its code, and that waits
+// for work already running on the device -- a request served on the cluster
+// tier while one-SM chains run would stall until they finish.
+void preload_kernels() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncAttributes a;
+    cudaFuncGetAttributes(&a, setup_pack_kernel);
+    cudaFuncGetAttributes(&a, setup_bprime_kernel);
+    cudaFuncGetAttributes(&a, setup_gram_kernel);
+    cudaFuncGetAttributes(&a, setup_delta_kernel);
+    const int smem = device_smem_optin();
+    // the limit covers dynamic shared memory only: the kernel's static part
+    // comes off the device's opt-in size
+    auto give_all = [smem](const void *k) {
+      cudaFuncAttributes fa;
+      if (cudaFuncGetAttributes(&fa, k) == cudaSuccess)
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem - (int)fa.sharedSizeBytes);
+    };
+    give_all((const void *)sa_tier1_kernel<kT1SmallThreads>);
+    give_all((const void *)sa_tier1_kernel<kT1LargeThreads>);
+    give_all((const void *)sa_batch_kernel);
+    give_all((const void *)sa_tier2_kernel);
+    give_all((const void *)sa_tier2_batch_kernel);
+    cudaFuncSetAttribute(sa_tier2_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(sa_tier2_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                         1);
+    cudaGetLastError();
+  });
+}
+
 int tier2_cluster(int N) {
   const int nt = (int)make_tiles(N, kT2R).size();
   return (nt + kT2Threads - 1) / kT2Threads;
 }
 
-int tier2_tpv(int N, int C) {
-  const int NV = (N + C - 1) / C;
-  int tpv = pow2_floor(kT2Threads / (NV > 0 ? NV : 1));
-  return tpv > 4 ? 4 : (tpv < 1 ? 1 : tpv);
-}
+int tier2_tpv(int, int) { return kT2Tpv; }
+
+int tier2_bytes(int N, int C) { return t2_layout(N, row_stride(N), C).bytes; }
 
 int tier2_fits(int N) {
   const int C = tier2_cluster(N);
-  if (C < 2 || C > kT2MaxCluster) return 0;
-  const int NV = (N + C - 1) / C;
-  const int vslots = (kT2Threads / 32) * (32 / tier2_tpv(N, C));
-  if (NV > 2 * vslots) return 0;
-  if (t2_layout(N).bytes > device_smem_optin()) return 0;
+  if (C < 2 || C > kT2MaxCluster || N > kT2MaxN) return 0;
+  if (tier2_bytes(N, C) + 64 > device_smem_optin()) return 0;  // 64: static part
   static int ok_for[kT2MaxCluster + 1] = {0};  // 0 unknown, 1 yes, -1 no
   if (ok_for[C] == 0) {
-    cudaFuncSetAttribute(sa_tier2_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(sa_tier2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         t2_layout(N).bytes);
+    preload_kernels();
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -229,7 +257,7 @@ int tier2_fits(int N) {
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(kT2Threads);
-    cfg.dynamicSmemBytes = t2_layout(N).bytes;
+    cfg.dynamicSmemBytes = tier2_bytes(N, C);
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
@@ -240,26 +268,6 @@ int tier2_fits(int N) {
   return ok_for[C] > 0;
 }
 
-// Load every kernel of the library now (once per process).  With lazy module
-// loading the first launch of a kernel loads its code, and that waits for work
-// already running on the device -- a request served on the cluster tier while
-// one-SM chains run would stall until they finish.
-void preload_kernels() {
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncAttributes a;
-    cudaFuncGetAttributes(&a, setup_pack_kernel);
-    cudaFuncGetAttributes(&a, setup_bprime_kernel);
-    cudaFuncGetAttributes(&a, setup_gram_kernel);
-    cudaFuncGetAttributes(&a, setup_delta_kernel);
-    cudaFuncGetAttributes(&a, sa_tier1_kernel<kT1SmallThreads>);
-    cudaFuncGetAttributes(&a, sa_tier1_kernel<kT1LargeThreads>);
-    cudaFuncGetAttributes(&a, sa_tier2_kernel);
-    cudaFuncGetAttributes(&a, sa_batch_kernel);
-    cudaFuncGetAttributes(&a, sa_tier2_batch_kernel);
-    cudaGetLastError();
-  });
-}
 
 int max_n_any() {
   static int cached = -1;
@@ -449,16 +457,7 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
     g.hyb_lo = (h->tier == 1) ? (e ? (float)atof(e) : 5e-4f) : 0.0f;
   }
   h->layout = t1_layout(N, S);
-  h->smem_bytes = h->tier == 1 ? h->layout.bytes : t2_layout(N).bytes;
-  if (h->tier == 2)
-    CKF(cudaFuncSetAttribute(sa_tier2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             h->smem_bytes));
-  else if (h->nthreads <= kT1SmallThreads)
-    CKF(cudaFuncSetAttribute(sa_tier1_kernel<kT1SmallThreads>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, h->layout.bytes));
-  else
-    CKF(cudaFuncSetAttribute(sa_tier1_kernel<kT1LargeThreads>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, h->layout.bytes));
+  h->smem_bytes = h->tier == 1 ? h->layout.bytes : tier2_bytes(N, h->cluster);
   CKF(cudaStreamSynchronize(stream));
   *out = h;
   return rc;
@@ -807,19 +806,6 @@ int qap_batch_create(const qap_problem *probs, int32_t count, qap_batch **out) {
   if ((e = cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * count,
                            cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
     return fail(e, "cudaMemcpyAsync");
-  if (b->n1 && (e = cudaFuncSetAttribute(sa_batch_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          b->smem)) != cudaSuccess)
-    return fail(e, "cudaFuncSetAttribute");
-  if (b->n2) {
-    if ((e = cudaFuncSetAttribute(sa_tier2_batch_kernel,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  b->smem2)) != cudaSuccess)
-      return fail(e, "cudaFuncSetAttribute");
-    if ((e = cudaFuncSetAttribute(sa_tier2_batch_kernel,
-                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
-      return fail(e, "cudaFuncSetAttribute");
-  }
   // The whole run is one graph: reset the work counters, then two persistent
   // launches side by side -- one CTA per chain for chains that fit one SM,
   // clusters for the others.

@@ -3,23 +3,26 @@
 // what one SM holds (up to ~1100).
 //
 // Where the data lives during a run:
-//   Delta  registers of the cluster: the R x 4 tiles of the upper triangle are
-//          split into C contiguous ranges, one per CTA (<= 640 tiles each);
-//   A, B'  global memory (int8 rows of stride S, L2-resident); CTA c owns the
-//          rows v of its slice [c*NV, (c+1)*NV) for the rows-r,s recompute and
-//          for the column swaps of B';
-//   a, b, d, p, the two recomputed rows, the threshold table: shared memory of
-//          every CTA (each CTA keeps its own copy and updates it identically).
+//   Delta  Tensor Memory of the cluster: the R x 4 tiles of the upper triangle
+//          are split into C contiguous ranges, one per CTA (<= 640 tiles each);
+//          thread t keeps its tile in its own TMEM lane, 4R columns, and moves
+//          it to registers 4 rows (16 cells) at a time;
+//   A, B'  shared memory of the cluster: CTA c holds the int8 rows v of its
+//          slice [c*NV, (c+1)*NV) of both matrices (row stride S), loaded once
+//          per launch; B' rows are written back at the end;
+//   a, b, d, p, the recomputed rows, rows r,s of A and B', the threshold
+//          table: shared memory of every CTA (each CTA keeps its own copy and
+//          updates it identically).
 //
-// One accepted swap costs two cluster barriers:
+// One accepted swap costs two cluster barriers and one CTA barrier:
 //   scan    each CTA tests its tiles in the window; warp winners post
 //           atomicMin(code) into every CTA's key word (DSMEM)  -> cluster barrier
-//   stage   (every CTA) a_k, b_k, d_k from rows r,s of B' before the swap
-//           || dot products of the rows-r,s recompute for this CTA's slice,
-//           on B' before the swap                            -> CTA barrier
-//   finish  rows r,s of this slice = dot products + O(1) corrections for the
-//           swap, posted into every CTA (DSMEM); O(1) update of the register
-//           cells                                            -> cluster barrier
+//   stage   (every CTA) rows r,s of A and of B' before the swap are read from
+//           the CTAs that own them (DSMEM) into local copies, and a_k, b_k,
+//           d_k, d_r, d_s formed from them                     -> CTA barrier
+//   finish  rows r,s of this slice from dot products over local shared memory
+//           plus O(1) corrections for the swap, posted into every CTA (DSMEM);
+//           O(1) update of the register cells                 -> cluster barrier
 // and at the top of the next scan each CTA swaps columns r,s of its B' rows (and
 // rewrites rows r,s if it owns them) and copies the recomputed rows into its
 // registers.  All control decisions are computed identically in every CTA from
@@ -29,6 +32,7 @@
 #include <cooperative_groups.h>
 
 #include "sa_tier1.cuh"
+#include "sa_tmem.cuh"
 
 namespace qapsa {
 
@@ -37,36 +41,58 @@ namespace cg = cooperative_groups;
 constexpr int kT2Threads = 640;
 constexpr int kT2R = 16;
 constexpr int kT2MaxCluster = 16;
+constexpr int kT2Tpv = 8;      // threads per slice row in the dot products
+constexpr int kT2MaxN = 1136;  // 16 CTAs x 640 tiles of 16 x 4 hold N <= 1136
+// TMEM columns a CTA allocates: the 20 warps share 4 lane groups, so five warps
+// use each lane group, 4R columns apiece (320), rounded up to a power of two.
+constexpr unsigned kT2TmemCols = 512;
+
+// Shared memory of one CTA.  Everything but the slices of A and B' sits at
+// fixed offsets sized for kT2MaxN, so that the compiler addresses it from the
+// base with immediates instead of holding a pointer per array in registers.
+constexpr int kT2NP = ((kT2MaxN + 15) & ~15) + 16;  // vector length bound
+constexpr int kT2MaxS = 1136;                       // row stride bound, 16 x odd
+constexpr int kT2OffCtl = 0;
+constexpr int kT2OffSlot = 128;
+constexpr int kT2OffTt = kT2OffSlot + 16 * 32 * kT2MaxCluster;
+constexpr int kT2OffVa = kT2OffTt + 8 * kTabMax;
+constexpr int kT2OffVb = kT2OffVa + 4 * kT2NP;
+constexpr int kT2OffVd = kT2OffVb + 4 * kT2NP;
+constexpr int kT2OffVp = kT2OffVd + 4 * kT2NP;
+constexpr int kT2OffVnr = kT2OffVp + 4 * kT2NP;
+constexpr int kT2OffVns = kT2OffVnr + 4 * kT2NP;
+constexpr int kT2OffRowAr = kT2OffVns + 4 * kT2NP;  // row r of A
+constexpr int kT2OffRowAs = kT2OffRowAr + kT2MaxS;  // row s of A
+constexpr int kT2OffRowBr = kT2OffRowAs + kT2MaxS;  // row r of B' before the swap
+constexpr int kT2OffRowBs = kT2OffRowBr + kT2MaxS;  // row s of B' before the swap
+constexpr int kT2OffSlice = kT2OffRowBs + kT2MaxS;  // this CTA's rows of A, then of B'
 
 struct T2Layout {
-  int off_a, off_b, off_d, off_p, off_nr, off_ns, off_or, off_os, off_slot, off_ctl, off_tt;
+  int NV;  // rows of A and B' per CTA
   int bytes;
 };
 
-__host__ __device__ inline T2Layout t2_layout(int N) {
-  const int NP = t1_vec_len(N);
+// Shared-memory size of one CTA of a C-CTA cluster (S: row stride, a multiple
+// of 16 bytes, <= kT2MaxS).
+__host__ __device__ inline T2Layout t2_layout(int N, int S, int C) {
   T2Layout L;
-  int o = 0;
-  L.off_a = o;    o += 4 * NP;
-  L.off_b = o;    o += 4 * NP;
-  L.off_d = o;    o += 4 * NP;
-  L.off_p = o;    o += 4 * NP;
-  L.off_nr = o;   o += 4 * NP;
-  L.off_ns = o;   o += 4 * NP;
-  L.off_or = o;   o += align16(NP);           // row r of B' before the swap
-  L.off_os = o;   o += align16(NP);           // row s of B' before the swap
-  L.off_slot = o; o += 16 * 32 * kT2MaxCluster;
-  L.off_ctl = o;  o += 128;
-  L.off_tt = o;   o += 8 * kTabMax;
-  L.bytes = o;
+  L.NV = (N + C - 1) / C;
+  L.bytes = kT2OffSlice + 2 * L.NV * S;
   return L;
+}
+
+// Byte i (0..3) of a packed word of int8 values, sign-extended.
+__device__ __forceinline__ int s8_of(int w, int i) {
+  return static_cast<int8_t>(static_cast<unsigned>(w) >> (8 * i));
 }
 
 // One chain on the calling cluster.  Every CTA of the cluster must call it with
 // the same arguments.
+// tb: TMEM address of the calling thread's tile (lane group of its warp,
+// first of the warp's 4R columns).
 __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
                                              unsigned long long it_end,
-                                             unsigned char *smem) {
+                                             unsigned char *smem, unsigned tb) {
   constexpr int R = kT2R;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -74,21 +100,25 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
   const int N = g.N, S = g.S, M = g.M;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthreads = blockDim.x;
-  const T2Layout L = t2_layout(N);
-  int *s_a = reinterpret_cast<int *>(smem + L.off_a);
-  int *s_b = reinterpret_cast<int *>(smem + L.off_b);
-  int *s_d = reinterpret_cast<int *>(smem + L.off_d);
-  int *s_p = reinterpret_cast<int *>(smem + L.off_p);
-  int *s_nr = reinterpret_cast<int *>(smem + L.off_nr);
-  int *s_ns = reinterpret_cast<int *>(smem + L.off_ns);
-  int8_t *s_or = reinterpret_cast<int8_t *>(smem + L.off_or);
-  int8_t *s_os = reinterpret_cast<int8_t *>(smem + L.off_os);
-  int4 *s_slot = reinterpret_cast<int4 *>(smem + L.off_slot);
-  unsigned *s_ctl = reinterpret_cast<unsigned *>(smem + L.off_ctl);
-  float2 *s_tt = reinterpret_cast<float2 *>(smem + L.off_tt);
+  const T2Layout L = t2_layout(N, S, C);
+  const int NV = L.NV;
+  int8_t *s_A = reinterpret_cast<int8_t *>(smem + kT2OffSlice);
+  int8_t *s_B = s_A + NV * S;
+  int *s_a = reinterpret_cast<int *>(smem + kT2OffVa);
+  int *s_b = reinterpret_cast<int *>(smem + kT2OffVb);
+  int *s_d = reinterpret_cast<int *>(smem + kT2OffVd);
+  int *s_p = reinterpret_cast<int *>(smem + kT2OffVp);
+  int *s_nr = reinterpret_cast<int *>(smem + kT2OffVnr);
+  int *s_ns = reinterpret_cast<int *>(smem + kT2OffVns);
+  int8_t *a_r = reinterpret_cast<int8_t *>(smem + kT2OffRowAr);
+  int8_t *a_s = reinterpret_cast<int8_t *>(smem + kT2OffRowAs);
+  int8_t *o_r = reinterpret_cast<int8_t *>(smem + kT2OffRowBr);
+  int8_t *o_s = reinterpret_cast<int8_t *>(smem + kT2OffRowBs);
+  int4 *s_slot = reinterpret_cast<int4 *>(smem + kT2OffSlot);
+  unsigned *s_ctl = reinterpret_cast<unsigned *>(smem + kT2OffCtl);
+  float2 *s_tt = reinterpret_cast<float2 *>(smem + kT2OffTt);
   unsigned long long *c64 = reinterpret_cast<unsigned long long *>(s_ctl + 8);
-  const int8_t *gA = g.A;
-  int8_t *gB = g.Bp;
+  const int sv_lo = rank * NV, sv_hi = min(N, sv_lo + NV);
 
   const int NP = t1_vec_len(N);
   for (int i = tid; i < NP; i += nthreads) {
@@ -96,6 +126,17 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     s_d[i] = i < N ? g.d[i] : 0;
     s_a[i] = 0;
     s_b[i] = 0;
+  }
+  {  // this CTA's rows of A and B'
+    const int n4 = max(0, sv_hi - sv_lo) * (S >> 4);
+    const int4 *gA4 = reinterpret_cast<const int4 *>(g.A + (size_t)sv_lo * S);
+    const int4 *gB4 = reinterpret_cast<const int4 *>(g.Bp + (size_t)sv_lo * S);
+    int4 *lA4 = reinterpret_cast<int4 *>(s_A);
+    int4 *lB4 = reinterpret_cast<int4 *>(s_B);
+    for (int i = tid; i < n4; i += nthreads) {
+      lA4[i] = __ldg(gA4 + i);
+      lB4[i] = gB4[i];
+    }
   }
   if (tid < 8) s_ctl[tid] = (tid < 3) ? kNone : 0u;
   if (tid == 0) {
@@ -116,25 +157,28 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     u0 = t >> 16;
     v0 = t & 0xFFFF;
   }
-  int D[R][4];
   int tm_lo = 0x7FFFFFFF, tm_hi = -1;
+#pragma unroll 1
+  for (int q = 0; q < R / 4; ++q) {  // cells to TMEM, 4 rows at a time
+    int Dq[16];
 #pragma unroll
-  for (int i = 0; i < R; ++i)
+    for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int u = u0 + i, v = v0 + c;
-      D[i][c] = 0;
-      if (has_tile && u < v && v < N) {
-        const int m = pidx(N, u, v);
-        D[i][c] = g.delta[m];
-        tm_lo = min(tm_lo, m);
-        tm_hi = max(tm_hi, m);
+      for (int c = 0; c < 4; ++c) {
+        const int u = u0 + 4 * q + ii, v = v0 + c;
+        Dq[4 * ii + c] = 0;
+        if (has_tile && u < v && v < N) {
+          const int m = pidx(N, u, v);
+          Dq[4 * ii + c] = g.delta[m];
+          tm_lo = min(tm_lo, m);
+          tm_hi = max(tm_hi, m);
+        }
       }
-    }
-  const int NV = (N + C - 1) / C;
-  const int sv_lo = rank * NV, sv_hi = min(N, sv_lo + NV);
+    tmem_st16(tb + 16 * q, Dq);
+  }
+  // dot products: tpv consecutive lanes per slice row, lpt rows per warp
   const int tpv = g.tpv, lpt = 32 / tpv;
-  const int t_sl = lane / lpt, v_l = lane - t_sl * lpt;
+  const int v_l = lane / tpv, t_sl = lane - v_l * tpv;
   const int vslots = (nthreads >> 5) * lpt;
   const int NC = S >> 4;
 
@@ -154,41 +198,53 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       // ---- B' swap of the previous accept (Eq. 3), this CTA's rows ----
       for (int v = sv_lo + tid; v < sv_hi; v += nthreads) {
         if (v == r || v == s) continue;
-        int8_t *row = gB + (size_t)v * S;
+        int8_t *row = s_B + (v - sv_lo) * S;
         const int8_t t = row[r];
         row[r] = row[s];
         row[s] = t;
       }
-      if (r >= sv_lo && r < sv_hi)  // new row r = old row s, columns r,s swapped
+      if (r >= sv_lo && r < sv_hi) {  // new row r = old row s, columns r,s swapped
+        int8_t *row = s_B + (r - sv_lo) * S;
         for (int k = tid; k < N; k += nthreads)
-          gB[(size_t)r * S + k] = (k == r) ? s_os[s] : (k == s ? s_os[r] : s_os[k]);
-      if (s >= sv_lo && s < sv_hi)  // new row s = old row r, columns r,s swapped
+          row[k] = (k == r) ? o_s[s] : (k == s ? o_s[r] : o_s[k]);
+      }
+      if (s >= sv_lo && s < sv_hi) {  // new row s = old row r, columns r,s swapped
+        int8_t *row = s_B + (s - sv_lo) * S;
         for (int k = tid; k < N; k += nthreads)
-          gB[(size_t)s * S + k] = (k == r) ? s_or[s] : (k == s ? s_or[r] : s_or[k]);
-      // ---- recomputed rows/columns r,s -> registers ----
-      if (has_tile) {
-        if ((r >= u0 && r < u0 + R) || (s >= u0 && s < u0 + R)) {
+          row[k] = (k == r) ? o_r[s] : (k == s ? o_r[r] : o_r[k]);
+      }
+      // ---- recomputed rows/columns r,s -> the TMEM cells (warp-collective) ----
+      const bool col_hit = has_tile && ((r >= v0 && r < v0 + 4) || (s >= v0 && s < v0 + 4));
+#pragma unroll 1
+      for (int q = 0; q < R / 4; ++q) {
+        const int uq = u0 + 4 * q;
+        const bool row_hit = has_tile && ((r >= uq && r < uq + 4) || (s >= uq && s < uq + 4));
+        if (!__any_sync(0xFFFFFFFFu, row_hit || col_hit)) continue;
+        int Dq[16];
+        tmem_ld16(tb + 16 * q, Dq);
+        if (row_hit) {
 #pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const int u = u0 + i;
+          for (int ii = 0; ii < 4; ++ii) {
+            const int u = uq + ii;
             if (u == r || u == s) {
               const int *src = (u == r) ? s_nr : s_ns;
 #pragma unroll
-              for (int c = 0; c < 4; ++c) D[i][c] = src[v0 + c];
+              for (int c = 0; c < 4; ++c) Dq[4 * ii + c] = src[v0 + c];
             }
           }
         }
-        if ((r >= v0 && r < v0 + 4) || (s >= v0 && s < v0 + 4)) {
+        if (col_hit) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const int v = v0 + c;
             if (v == r || v == s) {
               const int *src = (v == r) ? s_nr : s_ns;
 #pragma unroll
-              for (int i = 0; i < R; ++i) D[i][c] = src[u0 + i];
+              for (int ii = 0; ii < 4; ++ii) Dq[4 * ii + c] = src[uq + ii];
             }
           }
         }
+        tmem_st16(tb + 16 * q, Dq);
       }
     }
     pend_r = -1;
@@ -208,54 +264,70 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     }
     unsigned best = kNone;
     int bu = 0, bv = 0, bd = 0;
-    if (has_tile && meets_window(tm_lo, tm_hi, mb, wlen, M)) {
+    const bool scan_me = has_tile && meets_window(tm_lo, tm_hi, mb, wlen, M);
+    if (__any_sync(0xFFFFFFFFu, scan_me)) {
+#pragma unroll 1
+      for (int q = 0; q < R / 4; ++q) {
+        unsigned rows = 0;  // rows of this 4-row piece with a cell in the window
 #pragma unroll
-      for (int i = 0; i < R; ++i) {
-        const int u = u0 + i;
-        if (u >= N - 1 || u >= v0 + 3) continue;
-        const int mrow = u * N - (u * (u + 1)) / 2 - u - 1;
-        const int vlo = max(v0, u + 1), vhi = min(v0 + 3, N - 1);
-        if (!meets_window(mrow + vlo, mrow + vhi, mb, wlen, M)) continue;
-        int jc[4];
-        unsigned acc = 0, unc = 0, slow = 0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          int j = mrow + v0 + c - mb;
-          if (j < 0) j += M;
-          jc[c] = j;
-          const int v = v0 + c;
-          if (v > u && v < N && j < wlen) {
-            const int dv = D[i][c];
-            const int jt = jt0 + j;
-            if (dv <= 0) {
-              acc |= 1u << c;
-            } else if (jt < tab_len) {
-              const float2 b = s_tt[jt];
-              const float df = (float)dv;
-              if (df < b.x) acc |= 1u << c;
-              else if (!(df > b.y)) unc |= 1u << c;
-            } else if (dv <= thr) {
-              slow |= 1u << c;
-            }
+        for (int ii = 0; ii < 4; ++ii) {
+          const int u = u0 + 4 * q + ii;
+          if (scan_me && u < N - 1 && u < v0 + 3) {
+            const int mrow = u * N - (u * (u + 1)) / 2 - u - 1;
+            const int vlo = max(v0, u + 1), vhi = min(v0 + 3, N - 1);
+            if (meets_window(mrow + vlo, mrow + vhi, mb, wlen, M)) rows |= 1u << ii;
           }
         }
-        if (slow) {
-          const unsigned o = pretest_cells(g.seed, g.stream, g.log2a_f, g.mrel,
-                                           it, Tw, jc[0], jc[1], jc[2], jc[3],
-                                           D[i][0], D[i][1], D[i][2], D[i][3], slow);
-          acc |= o & 15u;
-          unc |= o >> 4;
-        }
-        const unsigned any = acc | unc;
+        if (!__any_sync(0xFFFFFFFFu, rows != 0u)) continue;
+        int Dq[16];
+        tmem_ld16(tb + 16 * q, Dq);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          if ((any >> c) & 1u) {
-            const unsigned key = ((unsigned)jc[c] << 1) | ((unc >> c) & 1u);
-            if (key < best) {
-              best = key;
-              bu = u;
-              bv = v0 + c;
-              bd = D[i][c];
+        for (int ii = 0; ii < 4; ++ii) {
+          if (!((rows >> ii) & 1u)) continue;
+          const int u = u0 + 4 * q + ii;
+          const int mrow = u * N - (u * (u + 1)) / 2 - u - 1;
+          int jc[4];
+          unsigned acc = 0, unc = 0, slow = 0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            int j = mrow + v0 + c - mb;
+            if (j < 0) j += M;
+            jc[c] = j;
+            const int v = v0 + c;
+            if (v > u && v < N && j < wlen) {
+              const int dv = Dq[4 * ii + c];
+              const int jt = jt0 + j;
+              if (dv <= 0) {
+                acc |= 1u << c;
+              } else if (jt < tab_len) {
+                const float2 b = s_tt[jt];
+                const float df = (float)dv;
+                if (df < b.x) acc |= 1u << c;
+                else if (!(df > b.y)) unc |= 1u << c;
+              } else if (dv <= thr) {
+                slow |= 1u << c;
+              }
+            }
+          }
+          if (slow) {
+            const unsigned o = pretest_cells(g.seed, g.stream, g.log2a_f, g.mrel, it, Tw,
+                                             jc[0], jc[1], jc[2], jc[3], Dq[4 * ii + 0],
+                                             Dq[4 * ii + 1], Dq[4 * ii + 2], Dq[4 * ii + 3],
+                                             slow);
+            acc |= o & 15u;
+            unc |= o >> 4;
+          }
+          const unsigned any = acc | unc;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if ((any >> c) & 1u) {
+              const unsigned key = ((unsigned)jc[c] << 1) | ((unc >> c) & 1u);
+              if (key < best) {
+                best = key;
+                bu = u;
+                bv = v0 + c;
+                bd = Dq[4 * ii + c];
+              }
             }
           }
         }
@@ -323,106 +395,113 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       c64[kC64Cost] += (unsigned long long)(long long)dlt;
     }
 
-    // ---- stage (every CTA): a, b, d from rows r,s of B' before the swap;
-    //      N may exceed the CTA's threads ----
-    int dr_part = 0, ds_part = 0;
-    for (int k = tid; k < N; k += nthreads) {
-      const int Ark = __ldg(gA + (size_t)r * S + k), Ask = __ldg(gA + (size_t)s * S + k);
-      const int Brk = __ldcg(gB + (size_t)r * S + k), Bsk = __ldcg(gB + (size_t)s * S + k);
-      s_or[k] = (int8_t)Brk;
-      s_os[k] = (int8_t)Bsk;
-      const int ak = Ark - Ask, bk = Bsk - Brk;
-      s_a[k] = 2 * ak;
-      s_b[k] = bk;
-      if (k != r && k != s) {
-        s_d[k] += ak * bk;
-        dr_part += Ark * Bsk;
-        ds_part += Ask * Brk;
-      } else if (k == s) {
-        dr_part += Ark * Brk;
-      } else {
-        ds_part += Ask * Bsk;
+    // ---- stage (every CTA): rows r,s of A and of B' before the swap from
+    //      the CTAs that own them; a, b, d, d_r, d_s from them ----
+    {
+      const int qr = r / NV, qs = s / NV;
+      const int *Ar = cluster.map_shared_rank(
+          reinterpret_cast<const int *>(s_A + (r - qr * NV) * S), qr);
+      const int *As = cluster.map_shared_rank(
+          reinterpret_cast<const int *>(s_A + (s - qs * NV) * S), qs);
+      const int *Br = cluster.map_shared_rank(
+          reinterpret_cast<const int *>(s_B + (r - qr * NV) * S), qr);
+      const int *Bs = cluster.map_shared_rank(
+          reinterpret_cast<const int *>(s_B + (s - qs * NV) * S), qs);
+      int *lAr = reinterpret_cast<int *>(a_r), *lAs = reinterpret_cast<int *>(a_s);
+      int *lBr = reinterpret_cast<int *>(o_r), *lBs = reinterpret_cast<int *>(o_s);
+      const int SW = S >> 2;
+      int dr_part = 0, ds_part = 0;
+      for (int w = tid; w < SW; w += nthreads) {
+        const int ar = Ar[w], as = As[w], br = Br[w], bs = Bs[w];
+        lAr[w] = ar;
+        lAs[w] = as;
+        lBr[w] = br;
+        lBs[w] = bs;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int k = 4 * w + i;
+          if (k < N) {
+            const int Ark = s8_of(ar, i), Ask = s8_of(as, i);
+            const int Brk = s8_of(br, i), Bsk = s8_of(bs, i);
+            const int ak = Ark - Ask, bk = Bsk - Brk;
+            s_a[k] = 2 * ak;
+            s_b[k] = bk;
+            if (k != r && k != s) {
+              s_d[k] += ak * bk;
+              dr_part += Ark * Bsk;
+              ds_part += Ask * Brk;
+            } else if (k == s) {
+              dr_part += Ark * Brk;
+            } else {
+              ds_part += Ask * Bsk;
+            }
+          }
+        }
       }
-      if (k == 0) {
+      if (tid == 0) {
         const int t = s_p[r];
         s_p[r] = s_p[s];
         s_p[s] = t;
       }
+      dr_part = __reduce_add_sync(0xFFFFFFFFu, dr_part);
+      ds_part = __reduce_add_sync(0xFFFFFFFFu, ds_part);
+      if (lane == 0 && (dr_part | ds_part)) {
+        atomicAdd(reinterpret_cast<int *>(s_ctl + kT1Dr), dr_part);
+        atomicAdd(reinterpret_cast<int *>(s_ctl + kT1Ds), ds_part);
+      }
     }
-    dr_part = __reduce_add_sync(0xFFFFFFFFu, dr_part);
-    ds_part = __reduce_add_sync(0xFFFFFFFFu, ds_part);
-    if (lane == 0 && (dr_part | ds_part)) {
-      atomicAdd(reinterpret_cast<int *>(s_ctl + kT1Dr), dr_part);
-      atomicAdd(reinterpret_cast<int *>(s_ctl + kT1Ds), ds_part);
-    }
-    // ---- dot products of this slice on B' before the swap ----
-    // slots: v = sv_lo + vb + warp * lpt + v_l for vb = 0, vslots, ...
-    constexpr int kMaxPass = 2;
-    int G1[kMaxPass], G2[kMaxPass], G3[kMaxPass], G4[kMaxPass];
+    __syncthreads();  // rows r,s, a, b, d, d_r, d_s complete
+
+    // ---- rows r,s of this slice under the new p, from dot products on B'
+    //      before the swap plus the O(1) terms the swap changes:
+    //      <A_r, B'new_v> = <A_r, B_v> + A_rs (B_vr - B_vs),
+    //      <A_v, B'new_r> = <A_v, B_s> + (A_vs - A_vr) B_rs, and symmetrically;
+    //      posted into every CTA ----
     {
-      const int4 *Ar4 = reinterpret_cast<const int4 *>(gA + (size_t)r * S);
-      const int4 *As4 = reinterpret_cast<const int4 *>(gA + (size_t)s * S);
-      const int4 *Br4 = reinterpret_cast<const int4 *>(gB + (size_t)r * S);
-      const int4 *Bs4 = reinterpret_cast<const int4 *>(gB + (size_t)s * S);
-#pragma unroll
-      for (int ps = 0; ps < kMaxPass; ++ps) {
-        const int v = sv_lo + ps * vslots + warp * lpt + v_l;
+      const int dr = (int)s_ctl[kT1Dr], ds = (int)s_ctl[kT1Ds];
+      const int Ars = a_r[s], Brs = o_r[s];
+      const int4 *Ar4 = reinterpret_cast<const int4 *>(a_r);
+      const int4 *As4 = reinterpret_cast<const int4 *>(a_s);
+      const int4 *Br4 = reinterpret_cast<const int4 *>(o_r);
+      const int4 *Bs4 = reinterpret_cast<const int4 *>(o_s);
+      for (int vb = 0; vb < sv_hi - sv_lo; vb += vslots) {
+        const int v = sv_lo + vb + warp * lpt + v_l;
         int g1 = 0, g2 = 0, g3 = 0, g4 = 0;
-        if (ps * vslots < sv_hi - sv_lo && v < sv_hi) {
-          const int4 *Av4 = reinterpret_cast<const int4 *>(gA + (size_t)v * S);
-          const int4 *Bv4 = reinterpret_cast<const int4 *>(gB + (size_t)v * S);
-#pragma unroll 2
+        if (v < sv_hi) {
+          const int4 *Av4 = reinterpret_cast<const int4 *>(s_A + (v - sv_lo) * S);
+          const int4 *Bv4 = reinterpret_cast<const int4 *>(s_B + (v - sv_lo) * S);
           for (int c = t_sl; c < NC; c += tpv) {
             const int4 bv = Bv4[c];
-            int4 x = __ldg(Ar4 + c);
+            int4 x = Ar4[c];
             g1 = __dp4a(x.x, bv.x, g1); g1 = __dp4a(x.y, bv.y, g1);
             g1 = __dp4a(x.z, bv.z, g1); g1 = __dp4a(x.w, bv.w, g1);
-            x = __ldg(As4 + c);
+            x = As4[c];
             g2 = __dp4a(x.x, bv.x, g2); g2 = __dp4a(x.y, bv.y, g2);
             g2 = __dp4a(x.z, bv.z, g2); g2 = __dp4a(x.w, bv.w, g2);
-            const int4 av = __ldg(Av4 + c);
-            x = __ldcg(Bs4 + c);
+            const int4 av = Av4[c];
+            x = Bs4[c];
             g3 = __dp4a(av.x, x.x, g3); g3 = __dp4a(av.y, x.y, g3);
             g3 = __dp4a(av.z, x.z, g3); g3 = __dp4a(av.w, x.w, g3);
-            x = __ldcg(Br4 + c);
+            x = Br4[c];
             g4 = __dp4a(av.x, x.x, g4); g4 = __dp4a(av.y, x.y, g4);
             g4 = __dp4a(av.z, x.z, g4); g4 = __dp4a(av.w, x.w, g4);
           }
         }
-        for (int o = lpt; o < 32; o <<= 1) {
+        for (int o = 1; o < tpv; o <<= 1) {
           g1 += __shfl_xor_sync(0xFFFFFFFFu, g1, o);
           g2 += __shfl_xor_sync(0xFFFFFFFFu, g2, o);
           g3 += __shfl_xor_sync(0xFFFFFFFFu, g3, o);
           g4 += __shfl_xor_sync(0xFFFFFFFFu, g4, o);
         }
-        G1[ps] = g1;
-        G2[ps] = g2;
-        G3[ps] = g3;
-        G4[ps] = g4;
-      }
-    }
-    __syncthreads();  // a, b, d, d_r, d_s and the staged rows are complete
-    const int dr = (int)s_ctl[kT1Dr], ds = (int)s_ctl[kT1Ds];
-
-    // ---- rows r,s of this slice under the new p, from the dot products on
-    //      B' before the swap plus the O(1) terms the swap changes:
-    //      <A_r, B'new_v> = <A_r, B_v> + A_rs (B_vr - B_vs),
-    //      <A_v, B'new_r> = <A_v, B_s> + (A_vs - A_vr) B_rs, and symmetrically ----
-    {
-      const int Ars = __ldg(gA + (size_t)r * S + s);
-      const int Brs = s_or[s];
-#pragma unroll
-      for (int ps = 0; ps < kMaxPass; ++ps) {
-        const int v = sv_lo + ps * vslots + warp * lpt + v_l;
-        if (t_sl == 0 && ps * vslots < sv_hi - sv_lo && v < sv_hi && v != r && v != s) {
-          const int Avr = __ldg(gA + (size_t)r * S + v), Avs = __ldg(gA + (size_t)s * S + v);
-          const int Bvr = s_or[v], Bvs = s_os[v];
+        if (v < sv_hi && v != r && v != s) {
+          const int Avr = a_r[v], Avs = a_s[v];
+          const int Bvr = o_r[v], Bvs = o_s[v];
           const int dv = s_d[v];
-          const int nr = 2 * (G1[ps] + Ars * (Bvr - Bvs) + G3[ps] + (Avs - Avr) * Brs -
+          const int nr = 2 * (g1 + Ars * (Bvr - Bvs) + g3 + (Avs - Avr) * Brs -
                               dr - dv + 2 * Avr * Bvs);
-          const int ns = 2 * (G2[ps] - Ars * (Bvr - Bvs) + G4[ps] - (Avs - Avr) * Brs -
+          const int ns = 2 * (g2 - Ars * (Bvr - Bvs) + g4 - (Avs - Avr) * Brs -
                               ds - dv + 2 * Avs * Bvr);
-          for (int q = 0; q < C; ++q) {
+          for (int q = t_sl; q < C; q += tpv) {
             cluster.map_shared_rank(s_nr, q)[v] = nr;
             cluster.map_shared_rank(s_ns, q)[v] = ns;
           }
@@ -449,24 +528,30 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
         }
       }
     }
-    // ---- O(1) update of the register cells ----
-    if (has_tile) {
+    // ---- O(1) update of the TMEM cells (warp-collective) ----
+    if (__any_sync(0xFFFFFFFFu, has_tile)) {
       const int4 av = *reinterpret_cast<const int4 *>(s_a + v0);
       const int4 bv = *reinterpret_cast<const int4 *>(s_b + v0);
+#pragma unroll 1
+      for (int q = 0; q < R / 4; ++q) {
+        int Dq[16];
+        tmem_ld16(tb + 16 * q, Dq);
 #pragma unroll
-      for (int i = 0; i < R; ++i) {
-        const int au = s_a[u0 + i], bu_ = s_b[u0 + i];
-        D[i][0] += (au - av.x) * (bv.x - bu_);
-        D[i][1] += (au - av.y) * (bv.y - bu_);
-        D[i][2] += (au - av.z) * (bv.z - bu_);
-        D[i][3] += (au - av.w) * (bv.w - bu_);
+        for (int ii = 0; ii < 4; ++ii) {
+          const int au = s_a[u0 + 4 * q + ii], bu_ = s_b[u0 + 4 * q + ii];
+          Dq[4 * ii + 0] += (au - av.x) * (bv.x - bu_);
+          Dq[4 * ii + 1] += (au - av.y) * (bv.y - bu_);
+          Dq[4 * ii + 2] += (au - av.z) * (bv.z - bu_);
+          Dq[4 * ii + 3] += (au - av.w) * (bv.w - bu_);
+        }
+        tmem_st16(tb + 16 * q, Dq);
       }
     }
     if (tid == 0) {
       s_nr[s] = -dlt;
       s_ns[r] = -dlt;
-      s_d[r] = dr;
-      s_d[s] = ds;
+      s_d[r] = (int)s_ctl[kT1Dr];
+      s_d[s] = (int)s_ctl[kT1Ds];
     }
     cluster.sync();  // rows r,s delivered everywhere; B' reads of this accept done
     if (tid == 0) {
@@ -478,14 +563,25 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
   }
 
   // ---- state back to global memory ----
+#pragma unroll 1
+  for (int q = 0; q < R / 4; ++q) {
+    int Dq[16];
+    tmem_ld16(tb + 16 * q, Dq);
 #pragma unroll
-  for (int i = 0; i < R; ++i)
+    for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int u = u0 + i, v = v0 + c;
-      if (has_tile && u < v && v < N) g.delta[pidx(N, u, v)] = D[i][c];
-    }
+      for (int c = 0; c < 4; ++c) {
+        const int u = u0 + 4 * q + ii, v = v0 + c;
+        if (has_tile && u < v && v < N) g.delta[pidx(N, u, v)] = Dq[4 * ii + c];
+      }
+  }
   __syncthreads();
+  {
+    const int n4 = max(0, sv_hi - sv_lo) * (S >> 4);
+    int4 *gB4 = reinterpret_cast<int4 *>(g.Bp + (size_t)sv_lo * S);
+    const int4 *lB4 = reinterpret_cast<const int4 *>(s_B);
+    for (int i = tid; i < n4; i += nthreads) gB4[i] = lB4[i];
+  }
   if (rank == 0) {
     for (int i = tid; i < N; i += nthreads) {
       g.p[i] = s_p[i];
@@ -504,10 +600,32 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
   cluster.sync();  // no CTA leaves while others may still address its memory
 }
 
+// TMEM for the calling CTA's tiles: allocated by warp 0, the address shared
+// through shared memory; each thread's tile address returned.
+__device__ __forceinline__ unsigned t2_tmem_acquire(unsigned *s_tmem) {
+  if (threadIdx.x < 32) tmem_alloc(s_tmem, kT2TmemCols);
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const int warp = (int)(threadIdx.x >> 5);
+  return tmem_warp_addr(*s_tmem, warp, (warp >> 2) * 4 * kT2R);
+}
+
+// Every TMEM access of the CTA done; warp 0 frees the columns.
+__device__ __forceinline__ void t2_tmem_release(const unsigned *s_tmem) {
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (threadIdx.x < 32) tmem_dealloc(*s_tmem, kT2TmemCols);
+}
+
 __global__ void __launch_bounds__(kT2Threads, 1)
     sa_tier2_kernel(ChainDev g, unsigned long long it_end) {
   extern __shared__ __align__(16) unsigned char smem[];
-  t2_run_chain(g, it_end, smem);
+  __shared__ unsigned s_tmem;
+  const unsigned tb = t2_tmem_acquire(&s_tmem);
+  t2_run_chain(g, it_end, smem, tb);
+  t2_tmem_release(&s_tmem);
 }
 
 // Batch of large chains: each cluster takes chains from a work list.
@@ -516,19 +634,20 @@ __global__ void __launch_bounds__(kT2Threads, 1)
                           const int *__restrict__ order, int n, int *counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_next;
+  __shared__ unsigned s_tmem;
   cg::cluster_group cluster = cg::this_cluster();
+  const unsigned tb = t2_tmem_acquire(&s_tmem);
   for (;;) {
     cluster.sync();
     if (cluster.block_rank() == 0 && threadIdx.x == 0) s_next = atomicAdd(counter, 1);
     cluster.sync();
     const int k = *cluster.map_shared_rank(&s_next, 0);
-    if (k >= n) {
-      cluster.sync();
-      return;
-    }
+    cluster.sync();  // every CTA has read the index before it can change
+    if (k >= n) break;
     const BatchChain &bc = chains[order[k]];
-    t2_run_chain(bc.g, bc.it_end, smem);
+    t2_run_chain(bc.g, bc.it_end, smem, tb);
   }
+  t2_tmem_release(&s_tmem);
 }
 
 }  // namespace qapsa

@@ -109,6 +109,29 @@ def test_run_splitting_is_invisible():
     assert_same(gs, os_, gd, od)
 
 
+def test_handles_of_different_sizes_interleave():
+    """A handle created after another, with a smaller (or larger) shared-memory
+    footprint on the same kernel, must not affect the other's launches."""
+    sizes = [230, 20, 320, 40]  # one-SM tier and cluster tier, large before small
+    I = 20000
+    chains, oracles = [], []
+    for k, N in enumerate(sizes):
+        A, B, p0 = instances.taixxa_like(N, 30 + k)
+        chains.append(sa.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=I, seed=k))
+        oracles.append(oracle.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=I, seed=k))
+    for half in range(2):
+        for g, o in zip(chains, oracles):
+            g.run(I // 2)
+            o.run(I // 2)
+    for g, o in zip(chains, oracles):
+        p, cost, acc = g.result()
+        st = o.state()
+        assert acc == st["accepts"] and cost == st["cost"]
+        assert np.array_equal(p, st["p"])
+        assert np.array_equal(g.delta().astype(np.int64), packed_upper(o.delta()))
+        g.close()
+
+
 def test_hot_limit_every_proposal_accepted():
     A, B, p0 = instances.taixxa_like(20, 3)
     I = 3000
