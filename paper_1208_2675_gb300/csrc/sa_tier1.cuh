@@ -2,9 +2,11 @@
 // and 3): one CTA runs the whole chain.
 //
 // Where the data lives during a run:
-//   Delta  registers: thread t owns an R x 4 tile of the upper triangle
-//          (rows u0..u0+R-1, columns v0..v0+3), so the O(1) update of a cell
-//          is three integer ops and the window scan reads registers;
+//   Delta  thread t owns an R x 4 tile of the upper triangle (rows
+//          u0..u0+R-1, columns v0..v0+3), in its registers (256 threads, up
+//          to 255 registers each) or, in the 640-thread kernels, in its own
+//          Tensor Memory lane, moved to registers 4 rows at a time; the O(1)
+//          update of a cell is three integer ops;
 //   A, B'  shared memory, int8, rows of stride S = 16 x odd bytes (conflict-free
 //          128-bit loads in the rows-r,s recompute);
 //   a, b, d, p, the two recomputed rows, per-warp winner slots: shared memory.
@@ -22,6 +24,7 @@
 // the next scan (each thread reads only its own registers there).
 #pragma once
 #include "sa_common.cuh"
+#include "sa_tmem.cuh"
 
 namespace qapsa {
 
@@ -184,6 +187,35 @@ __device__ __forceinline__ void t1_rebuild_tile(int (&D)[R][4], int u0, int v0,
     }
 }
 
+// The same for rows uq .. uq+3 of a tile (cells that are no pair get 0).
+__device__ __forceinline__ void t1_rebuild_piece(int (&Dq)[16], int uq, int v0, int N,
+                                                 int S, const int8_t *s_A,
+                                                 const int8_t *s_B, const int *s_d) {
+  const int NC = S >> 4;
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int u = uq + ii, v = v0 + c;
+      Dq[4 * ii + c] = 0;
+      if (!(u < v && v < N)) continue;
+      const int4 *Au = reinterpret_cast<const int4 *>(s_A + u * S);
+      const int4 *Bu = reinterpret_cast<const int4 *>(s_B + u * S);
+      const int4 *Av = reinterpret_cast<const int4 *>(s_A + v * S);
+      const int4 *Bv = reinterpret_cast<const int4 *>(s_B + v * S);
+      int guv = 0, gvu = 0;
+      for (int k = 0; k < NC; ++k) {
+        const int4 a = Au[k], b = Bv[k], a2 = Av[k], b2 = Bu[k];
+        guv = __dp4a(a.x, b.x, guv); guv = __dp4a(a.y, b.y, guv);
+        guv = __dp4a(a.z, b.z, guv); guv = __dp4a(a.w, b.w, guv);
+        gvu = __dp4a(a2.x, b2.x, gvu); gvu = __dp4a(a2.y, b2.y, gvu);
+        gvu = __dp4a(a2.z, b2.z, gvu); gvu = __dp4a(a2.w, b2.w, gvu);
+      }
+      Dq[4 * ii + c] =
+          2 * (guv + gvu - s_d[u] - s_d[v] + 2 * (int)s_A[u * S + v] * (int)s_B[u * S + v]);
+    }
+}
+
 // One chain, run by the whole CTA from its state in global memory to iteration
 // it_end and written back.  `smem` holds at least t1_layout(N, S).bytes.
 //
@@ -198,10 +230,13 @@ __device__ __forceinline__ void t1_rebuild_tile(int (&D)[R][4], int u0, int v0,
 // While many proposals are accepted (high temperature) direct mode is far
 // cheaper; the kernel switches to Delta mode, rebuilding Delta, once the
 // acceptance rate of a block of 16384 iterations drops below g.hyb_lo.
-template <int R>
+//
+// TM: the tiles live in TMEM at address tb (this thread's lane, 4R columns)
+// instead of registers; every TMEM access below is reached by whole warps.
+template <int R, bool TM>
 __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
                                              unsigned long long it_end,
-                                             unsigned char *smem) {
+                                             unsigned char *smem, unsigned tb) {
   const int N = g.N, S = g.S, M = g.M;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthreads = blockDim.x;
@@ -246,21 +281,42 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
     v0 = t & 0xFFFF;
   }
   // Cell (u0+i, v0+c) is a pair iff u0+i < v0+c < N.
-  int D[R][4];
+  int D[TM ? 1 : R][4];  // the register tiles (unused with TM)
   int tm_lo = 0x7FFFFFFF, tm_hi = -1;
+  if constexpr (TM) {
+#pragma unroll 1
+    for (int q = 0; q < R / 4; ++q) {
+      int Dq[16];
 #pragma unroll
-  for (int i = 0; i < R; ++i)
+      for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int u = u0 + i, v = v0 + c;
-      D[i][c] = 0;
-      if (has_tile && u < v && v < N) {
-        const int m = pidx(N, u, v);
-        D[i][c] = g.delta[m];
-        tm_lo = min(tm_lo, m);
-        tm_hi = max(tm_hi, m);
-      }
+        for (int c = 0; c < 4; ++c) {
+          const int u = u0 + 4 * q + ii, v = v0 + c;
+          Dq[4 * ii + c] = 0;
+          if (has_tile && u < v && v < N) {
+            const int m = pidx(N, u, v);
+            Dq[4 * ii + c] = g.delta[m];
+            tm_lo = min(tm_lo, m);
+            tm_hi = max(tm_hi, m);
+          }
+        }
+      tmem_st16(tb + 16 * q, Dq);
     }
+  } else {
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int u = u0 + i, v = v0 + c;
+        D[i][c] = 0;
+        if (has_tile && u < v && v < N) {
+          const int m = pidx(N, u, v);
+          D[i][c] = g.delta[m];
+          tm_lo = min(tm_lo, m);
+          tm_hi = max(tm_hi, m);
+        }
+      }
+  }
 
   unsigned long long *c64 = reinterpret_cast<unsigned long long *>(s_ctl + 8);
   if (tid == 0) {
@@ -301,28 +357,67 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
   __syncthreads();
 
   for (;;) {
-    // ---- rows/columns r,s recomputed by the previous accept -> registers ----
-    if (pend_r >= 0 && has_tile) {
-      const int r = pend_r, s = pend_s;
-      if ((r >= u0 && r < u0 + R) || (s >= u0 && s < u0 + R)) {
+    // ---- rows/columns r,s recomputed by the previous accept -> the tiles ----
+    if constexpr (TM) {
+      if (pend_r >= 0) {
+        const int r = pend_r, s = pend_s;
+        const bool col_hit = has_tile && ((r >= v0 && r < v0 + 4) || (s >= v0 && s < v0 + 4));
+#pragma unroll 1
+        for (int q = 0; q < R / 4; ++q) {
+          const int uq = u0 + 4 * q;
+          const bool row_hit =
+              has_tile && ((r >= uq && r < uq + 4) || (s >= uq && s < uq + 4));
+          if (!__any_sync(0xFFFFFFFFu, row_hit || col_hit)) continue;
+          int Dq[16];
+          tmem_ld16(tb + 16 * q, Dq);
+          if (row_hit) {
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const int u = u0 + i;
-          if (u == r || u == s) {
-            const int *src = (u == r) ? s_nr : s_ns;
+            for (int ii = 0; ii < 4; ++ii) {
+              const int u = uq + ii;
+              if (u == r || u == s) {
+                const int *src = (u == r) ? s_nr : s_ns;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) D[i][c] = src[v0 + c];
+                for (int c = 0; c < 4; ++c) Dq[4 * ii + c] = src[v0 + c];
+              }
+            }
           }
+          if (col_hit) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int v = v0 + c;
+              if (v == r || v == s) {
+                const int *src = (v == r) ? s_nr : s_ns;
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii) Dq[4 * ii + c] = src[uq + ii];
+              }
+            }
+          }
+          tmem_st16(tb + 16 * q, Dq);
         }
       }
-      if ((r >= v0 && r < v0 + 4) || (s >= v0 && s < v0 + 4)) {
+    } else {
+      if (pend_r >= 0 && has_tile) {
+        const int r = pend_r, s = pend_s;
+        if ((r >= u0 && r < u0 + R) || (s >= u0 && s < u0 + R)) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int v = v0 + c;
-          if (v == r || v == s) {
-            const int *src = (v == r) ? s_nr : s_ns;
+          for (int i = 0; i < R; ++i) {
+            const int u = u0 + i;
+            if (u == r || u == s) {
+              const int *src = (u == r) ? s_nr : s_ns;
 #pragma unroll
-            for (int i = 0; i < R; ++i) D[i][c] = src[u0 + i];
+              for (int c = 0; c < 4; ++c) D[i][c] = src[v0 + c];
+            }
+          }
+        }
+        if ((r >= v0 && r < v0 + 4) || (s >= v0 && s < v0 + 4)) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int v = v0 + c;
+            if (v == r || v == s) {
+              const int *src = (v == r) ? s_nr : s_ns;
+#pragma unroll
+              for (int i = 0; i < R; ++i) D[i][c] = src[u0 + i];
+            }
           }
         }
       }
@@ -331,8 +426,18 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
     // Delta registers from their definition: after a switch to Delta mode, and
     // before the state is stored if Delta was not being maintained.
     const bool last = it >= it_end || err;
-    if (has_tile && (rebuild || (last && mode == 1)))
+    if constexpr (TM) {
+      if (rebuild || (last && mode == 1)) {
+#pragma unroll 1
+        for (int q = 0; q < R / 4; ++q) {
+          int Dq[16];
+          t1_rebuild_piece(Dq, u0 + 4 * q, v0, has_tile ? N : 0, S, s_A, s_B, s_d);
+          tmem_st16(tb + 16 * q, Dq);
+        }
+      }
+    } else if (has_tile && (rebuild || (last && mode == 1))) {
       t1_rebuild_tile<R>(D, u0, v0, N, S, s_A, s_B, s_d);
+    }
     rebuild = false;
     if (last) break;
 
@@ -412,6 +517,76 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
               bu = r;
               bv = s;
               bd = dv;
+            }
+          }
+        }
+      }
+    } else if constexpr (TM) {
+      const bool scan_me = has_tile && meets_window(tm_lo, tm_hi, mb, wlen, M);
+      if (__any_sync(0xFFFFFFFFu, scan_me)) {
+#pragma unroll 1
+        for (int q = 0; q < R / 4; ++q) {
+          unsigned rows = 0;  // rows of this 4-row piece with a cell in the window
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) {
+            const int u = u0 + 4 * q + ii;
+            if (scan_me && u < N - 1 && u < v0 + 3) {
+              const int mrow = u * N - (u * (u + 1)) / 2 - u - 1;
+              const int vlo = max(v0, u + 1), vhi = min(v0 + 3, N - 1);
+              if (meets_window(mrow + vlo, mrow + vhi, mb, wlen, M)) rows |= 1u << ii;
+            }
+          }
+          if (!__any_sync(0xFFFFFFFFu, rows != 0u)) continue;
+          int Dq[16];
+          tmem_ld16(tb + 16 * q, Dq);
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) {
+            if (!((rows >> ii) & 1u)) continue;
+            const int u = u0 + 4 * q + ii;
+            const int mrow = u * N - (u * (u + 1)) / 2 - u - 1;
+            int jc[4];
+            unsigned acc = 0, unc = 0, slow = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              int j = mrow + v0 + c - mb;
+              if (j < 0) j += M;
+              jc[c] = j;
+              const int v = v0 + c;
+              if (v > u && v < N && j < wlen) {
+                const int dv = Dq[4 * ii + c];
+                const int jt = jt0 + j;
+                if (dv <= 0) {
+                  acc |= 1u << c;
+                } else if (jt < tab_len) {
+                  const float2 b = s_tt[jt];
+                  const float df = (float)dv;
+                  if (df < b.x) acc |= 1u << c;
+                  else if (!(df > b.y)) unc |= 1u << c;
+                } else if (dv <= thr) {
+                  slow |= 1u << c;
+                }
+              }
+            }
+            if (slow) {
+              const unsigned o = pretest_cells(g.seed, g.stream, g.log2a_f, g.mrel, it, Tw,
+                                               jc[0], jc[1], jc[2], jc[3], Dq[4 * ii + 0],
+                                               Dq[4 * ii + 1], Dq[4 * ii + 2],
+                                               Dq[4 * ii + 3], slow);
+              acc |= o & 15u;
+              unc |= o >> 4;
+            }
+            const unsigned any = acc | unc;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              if ((any >> c) & 1u) {
+                const unsigned key = ((unsigned)jc[c] << 1) | ((unc >> c) & 1u);
+                if (key < best) {
+                  best = key;
+                  bu = u;
+                  bv = v0 + c;
+                  bd = Dq[4 * ii + c];
+                }
+              }
             }
           }
         }
@@ -664,18 +839,39 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
         }
       }
     }
-    // ---- O(1) update of every register cell: Delta_uv += 2 (a_u - a_v)(b_v - b_u);
+    // ---- O(1) update of every tile cell: Delta_uv += 2 (a_u - a_v)(b_v - b_u);
     //      cells in rows/columns r,s are overwritten from s_nr/s_ns later ----
-    if (has_tile) {
-      const int4 av = *reinterpret_cast<const int4 *>(s_a + v0);
-      const int4 bv = *reinterpret_cast<const int4 *>(s_b + v0);
+    if constexpr (TM) {
+      if (__any_sync(0xFFFFFFFFu, has_tile)) {
+        const int4 av = *reinterpret_cast<const int4 *>(s_a + v0);
+        const int4 bv = *reinterpret_cast<const int4 *>(s_b + v0);
+#pragma unroll 1
+        for (int q = 0; q < R / 4; ++q) {
+          int Dq[16];
+          tmem_ld16(tb + 16 * q, Dq);
 #pragma unroll
-      for (int i = 0; i < R; ++i) {
-        const int au = s_a[u0 + i], bu_ = s_b[u0 + i];
-        D[i][0] += (au - av.x) * (bv.x - bu_);
-        D[i][1] += (au - av.y) * (bv.y - bu_);
-        D[i][2] += (au - av.z) * (bv.z - bu_);
-        D[i][3] += (au - av.w) * (bv.w - bu_);
+          for (int ii = 0; ii < 4; ++ii) {
+            const int au = s_a[u0 + 4 * q + ii], bu_ = s_b[u0 + 4 * q + ii];
+            Dq[4 * ii + 0] += (au - av.x) * (bv.x - bu_);
+            Dq[4 * ii + 1] += (au - av.y) * (bv.y - bu_);
+            Dq[4 * ii + 2] += (au - av.z) * (bv.z - bu_);
+            Dq[4 * ii + 3] += (au - av.w) * (bv.w - bu_);
+          }
+          tmem_st16(tb + 16 * q, Dq);
+        }
+      }
+    } else {
+      if (has_tile) {
+        const int4 av = *reinterpret_cast<const int4 *>(s_a + v0);
+        const int4 bv = *reinterpret_cast<const int4 *>(s_b + v0);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          const int au = s_a[u0 + i], bu_ = s_b[u0 + i];
+          D[i][0] += (au - av.x) * (bv.x - bu_);
+          D[i][1] += (au - av.y) * (bv.y - bu_);
+          D[i][2] += (au - av.z) * (bv.z - bu_);
+          D[i][3] += (au - av.w) * (bv.w - bu_);
+        }
       }
     }
     }
@@ -714,13 +910,28 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
   }
 
   // ---- state back to global memory ----
+  if constexpr (TM) {
+#pragma unroll 1
+    for (int q = 0; q < R / 4; ++q) {
+      int Dq[16];
+      tmem_ld16(tb + 16 * q, Dq);
 #pragma unroll
-  for (int i = 0; i < R; ++i)
+      for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int u = u0 + i, v = v0 + c;
-      if (has_tile && u < v && v < N) g.delta[pidx(N, u, v)] = D[i][c];
+        for (int c = 0; c < 4; ++c) {
+          const int u = u0 + 4 * q + ii, v = v0 + c;
+          if (has_tile && u < v && v < N) g.delta[pidx(N, u, v)] = Dq[4 * ii + c];
+        }
     }
+  } else {
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int u = u0 + i, v = v0 + c;
+        if (has_tile && u < v && v < N) g.delta[pidx(N, u, v)] = D[i][c];
+      }
+  }
   __syncthreads();
   {
     const int4 *sB = reinterpret_cast<const int4 *>(s_B);
@@ -749,7 +960,14 @@ template <int BOUND>
 __global__ void __launch_bounds__(BOUND, 1)
     sa_tier1_kernel(ChainDev g, unsigned long long it_end) {
   extern __shared__ __align__(16) unsigned char smem[];
-  t1_run_chain<kT1R>(g, it_end, smem);
+  if constexpr (BOUND > kT1SmallThreads) {  // 96 registers a thread: tiles in TMEM
+    __shared__ unsigned s_tmem;
+    const unsigned tb = tile_tmem_acquire(&s_tmem, 4 * kT1R);
+    t1_run_chain<kT1R, true>(g, it_end, smem, tb);
+    tile_tmem_release(&s_tmem);
+  } else {
+    t1_run_chain<kT1R, false>(g, it_end, smem, 0u);
+  }
 }
 
 // ------------------------------------------------------------------------- //
@@ -773,15 +991,18 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
                     const int *__restrict__ order, int n, int *counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_next;
+  __shared__ unsigned s_tmem;
+  const unsigned tb = tile_tmem_acquire(&s_tmem, 4 * kT1R);
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
     __syncthreads();
     const int k = s_next;
-    if (k >= n) return;
+    if (k >= n) break;
     const BatchChain &bc = chains[order[k]];
-    t1_run_chain<kT1R>(bc.g, bc.it_end, smem);
+    t1_run_chain<kT1R, true>(bc.g, bc.it_end, smem, tb);
   }
+  tile_tmem_release(&s_tmem);
 }
 
 }  // namespace qapsa

@@ -43,9 +43,6 @@ constexpr int kT2R = 16;
 constexpr int kT2MaxCluster = 16;
 constexpr int kT2Tpv = 8;      // threads per slice row in the dot products
 constexpr int kT2MaxN = 1136;  // 16 CTAs x 640 tiles of 16 x 4 hold N <= 1136
-// TMEM columns a CTA allocates: the 20 warps share 4 lane groups, so five warps
-// use each lane group, 4R columns apiece (320), rounded up to a power of two.
-constexpr unsigned kT2TmemCols = 512;
 
 // Shared memory of one CTA.  Everything but the slices of A and B' sits at
 // fixed offsets sized for kT2MaxN, so that the compiler addresses it from the
@@ -600,32 +597,13 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
   cluster.sync();  // no CTA leaves while others may still address its memory
 }
 
-// TMEM for the calling CTA's tiles: allocated by warp 0, the address shared
-// through shared memory; each thread's tile address returned.
-__device__ __forceinline__ unsigned t2_tmem_acquire(unsigned *s_tmem) {
-  if (threadIdx.x < 32) tmem_alloc(s_tmem, kT2TmemCols);
-  tmem_fence_before_sync();
-  __syncthreads();
-  tmem_fence_after_sync();
-  const int warp = (int)(threadIdx.x >> 5);
-  return tmem_warp_addr(*s_tmem, warp, (warp >> 2) * 4 * kT2R);
-}
-
-// Every TMEM access of the CTA done; warp 0 frees the columns.
-__device__ __forceinline__ void t2_tmem_release(const unsigned *s_tmem) {
-  tmem_fence_before_sync();
-  __syncthreads();
-  tmem_fence_after_sync();
-  if (threadIdx.x < 32) tmem_dealloc(*s_tmem, kT2TmemCols);
-}
-
 __global__ void __launch_bounds__(kT2Threads, 1)
     sa_tier2_kernel(ChainDev g, unsigned long long it_end) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_tmem;
-  const unsigned tb = t2_tmem_acquire(&s_tmem);
+  const unsigned tb = tile_tmem_acquire(&s_tmem, 4 * kT2R);
   t2_run_chain(g, it_end, smem, tb);
-  t2_tmem_release(&s_tmem);
+  tile_tmem_release(&s_tmem);
 }
 
 // Batch of large chains: each cluster takes chains from a work list.
@@ -636,7 +614,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
   __shared__ int s_next;
   __shared__ unsigned s_tmem;
   cg::cluster_group cluster = cg::this_cluster();
-  const unsigned tb = t2_tmem_acquire(&s_tmem);
+  const unsigned tb = tile_tmem_acquire(&s_tmem, 4 * kT2R);
   for (;;) {
     cluster.sync();
     if (cluster.block_rank() == 0 && threadIdx.x == 0) s_next = atomicAdd(counter, 1);
@@ -647,7 +625,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
     const BatchChain &bc = chains[order[k]];
     t2_run_chain(bc.g, bc.it_end, smem, tb);
   }
-  t2_tmem_release(&s_tmem);
+  tile_tmem_release(&s_tmem);
 }
 
 }  // namespace qapsa

@@ -81,4 +81,32 @@ __device__ __forceinline__ void tmem_st16(unsigned taddr, const int (&v)[16]) {
       : "memory");
 }
 
+// Columns a CTA of the SA kernels allocates: all 512.  With 64 columns a thread
+// (one 16 x 4 tile) and warps w, w+4, w+8, ... sharing a lane group, a block of
+// up to 1024 threads fits.  Only one such CTA is resident on an SM: they all run
+// 640 threads at more than 51 registers each, or (the cluster kernels) use more
+// than half of the SM's shared memory; a second CTA that asked for TMEM would
+// wait in tcgen05.alloc until the first one freed it.
+constexpr unsigned kTileTmemCols = 512;
+
+// TMEM for the calling CTA's tiles: allocated by warp 0, the address passed
+// through shared memory; returns the address of this thread's tile
+// (cols_per_thread consecutive columns of its lane).
+__device__ __forceinline__ unsigned tile_tmem_acquire(unsigned *s_tmem, int cols_per_thread) {
+  if (threadIdx.x < 32) tmem_alloc(s_tmem, kTileTmemCols);
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const int warp = (int)(threadIdx.x >> 5);
+  return tmem_warp_addr(*s_tmem, warp, (warp >> 2) * cols_per_thread);
+}
+
+// Every TMEM access of the CTA is done; warp 0 frees the columns.
+__device__ __forceinline__ void tile_tmem_release(const unsigned *s_tmem) {
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (threadIdx.x < 32) tmem_dealloc(*s_tmem, kTileTmemCols);
+}
+
 }  // namespace qapsa
