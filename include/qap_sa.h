@@ -129,10 +129,11 @@ QAP_EXPORT int qap_sa_result_device(qap_sa *h, int32_t *p_out, int64_t *cost,
 /* Diagnostics of the current state (after a stream sync). */
 typedef struct qap_sa_info {
   int32_t N;
-  int32_t tier;           /* 1 = one CTA (Delta in its registers, A and B' in
-                             its shared memory); 2 = a thread-block cluster
-                             (Delta in the cluster's registers, A and B' in
-                             global memory), for N beyond one SM           */
+  int32_t tier;           /* 1 = one CTA (Delta in its registers or its
+                             Tensor Memory, A and B' in its shared memory);
+                             2 = a thread-block cluster (Delta in the
+                             cluster's Tensor Memory, A and B' split over the
+                             cluster's shared memory), for N beyond one SM */
   uint64_t iterations;    /* it: iterations done                            */
   uint64_t accepts;
   int64_t cost;
@@ -145,6 +146,8 @@ typedef struct qap_sa_info {
   uint64_t direct_iters;  /* iterations whose proposal was evaluated directly
                              (high acceptance) instead of read from Delta  */
   uint64_t direct_accepts;/* accepted swaps among them (no Delta update)    */
+  uint64_t warp_iters;    /* direct iterations run by one warp alone, with no
+                             block barrier (acceptance rate >= 1/256)       */
 } qap_sa_info;
 QAP_EXPORT int qap_sa_get_info(qap_sa *h, qap_sa_info *out);
 

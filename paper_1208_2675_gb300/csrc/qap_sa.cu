@@ -451,10 +451,14 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   g.mrel = (float)(2e-5 + 2e-7 * fabs(l2r) + 8.0 * (double)sc->total_iters * 0x1p-53);
   // Acceptance rate below which the one-SM tier maintains Delta (above it,
   // proposals are evaluated directly): where one accepted swap's O(N^2) update
-  // costs as much as evaluating ~2000 proposals directly.
+  // costs as much as evaluating ~2000 proposals directly.  From one accept in
+  // 256 proposals up, one warp evaluates them alone (windows of 32..128, no
+  // block barrier per accepted swap).
   {
     const char *e = getenv("QAPSA_HYBRID_RATE");
     g.hyb_lo = (h->tier == 1) ? (e ? (float)atof(e) : 5e-4f) : 0.0f;
+    const char *ew = getenv("QAPSA_WARP_RATE");
+    g.warp_lo = (h->tier == 1) ? (ew ? (float)atof(ew) : 1.0f / 256.0f) : 0.0f;
   }
   h->layout = t1_layout(N, S);
   h->smem_bytes = h->tier == 1 ? h->layout.bytes : tier2_bytes(N, h->cluster);
@@ -644,6 +648,7 @@ int qap_sa_get_info(qap_sa *h, qap_sa_info *out) {
   out->smem_bytes = (uint64_t)h->smem_bytes;
   out->direct_iters = st.direct_iters;
   out->direct_accepts = st.direct_accepts;
+  out->warp_iters = st.warp_iters;
   return st.error ? QAP_E_STATE : QAP_OK;
 }
 

@@ -32,6 +32,7 @@ struct ChainStatus {
   int mode;                       // 1: proposals evaluated directly, 0: from Delta
   unsigned long long direct_iters;    // iterations whose proposal was evaluated directly
   unsigned long long direct_accepts;  // accepted swaps among them
+  unsigned long long warp_iters;      // direct iterations run by one warp alone
 };
 
 // Everything one chain's kernels need (passed by value).
@@ -56,6 +57,8 @@ struct ChainDev {
   float log2a_f;     // log2(alpha)
   float mrel;        // relative margin of the approximate pre-test
   float hyb_lo;      // acceptance rate below which Delta is maintained (0: always)
+  float warp_lo;     // acceptance rate from which one warp runs direct mode alone
+                     // (0: never)
 };
 
 // ------------------------------------------------------------------------- //

@@ -74,7 +74,14 @@ constexpr int kT1LargeThreads = 640;
 // 8-byte aligned) thread 0's 64-bit counters.
 enum : int { kT1Key0 = 0, kT1Dr = 3, kT1Ds = 4, kT1Dec = 5, kT1Dr1 = 6, kT1Ds1 = 7 };
 enum : int { kC64Accepts = 0, kC64Cost = 1, kC64Near = 2, kC64Exact = 3, kC64Windows = 4,
-              kC64DirIt = 5, kC64DirAcc = 6 };
+              kC64DirIt = 5, kC64DirAcc = 6, kC64WarpIt = 7 };
+// s_ctl words 24..31: the chain position handed between the CTA and the
+// warp-only direct mode.
+constexpr int kT1Pos = 24;
+// Iterations per block of the mode decisions (Delta / direct / warp-only).
+constexpr int kHybBlock = 16384;
+// Longest window of the warp-only direct mode.
+constexpr int kWarpMaxK = 128;
 
 __device__ __forceinline__ float u64_to_f32(unsigned long long x) {
   return __uint2float_rn((unsigned)(x >> 32)) * 4294967296.0f +
@@ -216,6 +223,257 @@ __device__ __forceinline__ void t1_rebuild_piece(int (&Dq)[16], int uq, int v0, 
     }
 }
 
+struct WarpPos {
+  unsigned it_lo, it_hi;
+  int mb, cr, cs, blk_it, blk_acc, err;
+};
+
+// Byte i (0..3) of a packed word of int8 values, sign-extended.
+__device__ __forceinline__ int s8_of(int w, int i) {
+  return static_cast<int8_t>(static_cast<unsigned>(w) >> (8 * i));
+}
+
+// Product of 16 int8 pairs (two 16-byte chunks) added to acc.
+__device__ __forceinline__ int dot16x(int4 x, int4 y, int acc) {
+  acc = __dp4a(x.x, y.x, acc);
+  acc = __dp4a(x.y, y.y, acc);
+  acc = __dp4a(x.z, y.z, acc);
+  return __dp4a(x.w, y.w, acc);
+}
+
+// Direct mode run by the calling warp alone, with no block barrier: while
+// proposals are accepted often, an accepted swap then costs a few hundred
+// cycles of one warp.  Lane l evaluates proposal it + j, j = l, l + 32, ... of a
+// window of up to kWarpMaxK proposals -- delta = 2 (<A_r, B'_s> + <A_s, B'_r>
+// - d_r - d_s + 2 A_rs B'_rs) by dp4a, its Eq. (2) pre-test from its own
+// Philox block -- the first accepted one is found with a warp reduction, and
+// the swap is applied to B', d and p by the lanes together.  The chain
+// position comes from and goes back to *pos; returns at it_end, at the end of
+// the current block of kHybBlock iterations, or on an inconsistency.  Counters
+// go to c64 (lane 0).
+__device__ __noinline__ void t1_warp_direct(int N, int S, int M, unsigned long long seed,
+                                            unsigned stream, double T0, const double *P,
+                                            float T0f, float log2a_f, float mrel,
+                                            unsigned long long it_end,
+                                            const int8_t *s_A, int8_t *s_B, int *s_d,
+                                            int *s_p, unsigned long long *c64,
+                                            WarpPos *pos) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  const int NC = S >> 4;
+  __syncwarp();
+  unsigned long long it = ((unsigned long long)pos->it_hi << 32) | pos->it_lo;
+  int mb = pos->mb, cr = pos->cr, cs = pos->cs;
+  int blk_it = pos->blk_it, blk_acc = pos->blk_acc, err = 0;
+  // counters of this call (lane 0 adds them to c64 at the end)
+  unsigned long long n_it = 0, n_acc = 0, n_win = 0, n_exact = 0;
+  long long d_cost = 0;
+  const int kmax = min(M, kWarpMaxK);
+  int K = min(32, kmax);
+  // Rolling table of Eq. (2) pre-test intervals in registers: lane l holds
+  // those of Philox block q0 + l (iterations 4 (q0 + l) .. + 3), computed as the
+  // prepared table computes them; a proposal fetches its own by shuffles.
+  unsigned long long q0 = ~0ull;
+  float2 tb0 = make_float2(0.f, 0.f), tb1 = tb0, tb2 = tb0, tb3 = tb0;
+  while (it < it_end && blk_it < kHybBlock) {
+    const int wlen = (int)min((unsigned long long)K, it_end - it);
+    unsigned best = kNone;
+    int brs = 0, bdv = 0;
+    for (int j0 = 0; j0 < wlen; j0 += 32) {
+      {
+        const unsigned long long qa = (it + (unsigned)j0) >> 2;
+        if (qa < q0 || ((it + (unsigned)j0 + 31u) >> 2) >= q0 + 32) {  // refill
+          q0 = qa;
+          const unsigned long long q = q0 + (unsigned)lane;
+          const uint4 x = rng_block(seed, stream, q);
+          const float Tq = T0f * exp2f(u64_to_f32(q << 2) * log2a_f);
+          tb0 = accept_interval(mrel, Tq, x.x);
+          tb1 = accept_interval(mrel, Tq * exp2f(log2a_f), x.y);
+          tb2 = accept_interval(mrel, Tq * exp2f(2.0f * log2a_f), x.z);
+          tb3 = accept_interval(mrel, Tq * exp2f(3.0f * log2a_f), x.w);
+        }
+      }
+      const int j = j0 + lane;
+      float2 b;
+      {
+        const unsigned long long itc = it + (unsigned)j;
+        const int src = (int)((itc >> 2) - q0) & 31, w = (int)(itc & 3u);
+        const float x0 = __shfl_sync(FULL, tb0.x, src), y0 = __shfl_sync(FULL, tb0.y, src);
+        const float x1 = __shfl_sync(FULL, tb1.x, src), y1 = __shfl_sync(FULL, tb1.y, src);
+        const float x2 = __shfl_sync(FULL, tb2.x, src), y2 = __shfl_sync(FULL, tb2.y, src);
+        const float x3 = __shfl_sync(FULL, tb3.x, src), y3 = __shfl_sync(FULL, tb3.y, src);
+        b.x = w == 0 ? x0 : (w == 1 ? x1 : (w == 2 ? x2 : x3));
+        b.y = w == 0 ? y0 : (w == 1 ? y1 : (w == 2 ? y2 : y3));
+      }
+      if (j < wlen) {
+        int r = cr, s = cs + j;
+        while (s >= N) {  // on into the next rows of the cyclic order
+          const int o = s - N;
+          if (++r >= N - 1) r = 0;
+          s = r + 1 + o;
+        }
+        const int4 *Ar4 = reinterpret_cast<const int4 *>(s_A + r * S);
+        const int4 *As4 = reinterpret_cast<const int4 *>(s_A + s * S);
+        const int4 *Br4 = reinterpret_cast<const int4 *>(s_B + r * S);
+        const int4 *Bs4 = reinterpret_cast<const int4 *>(s_B + s * S);
+        int g1 = 0, g2 = 0;
+#pragma unroll 4
+        for (int c = 0; c < NC; ++c) {
+          g1 = dot16x(Ar4[c], Bs4[c], g1);
+          g2 = dot16x(As4[c], Br4[c], g2);
+        }
+        const int dv = 2 * (g1 + g2 - s_d[r] - s_d[s] +
+                            2 * (int)s_A[r * S + s] * (int)s_B[r * S + s]);
+        const float df = (float)dv;
+        const unsigned acc = (dv <= 0 || df < b.x) ? 1u : 0u;
+        const unsigned unc = (!acc && !(df > b.y)) ? 1u : 0u;
+        if (acc | unc) {
+          best = ((unsigned)j << 1) | unc;
+          brs = (r << 16) | s;
+          bdv = dv;
+        }
+      }
+      if (__any_sync(FULL, best != kNone)) break;  // later passes come later in order
+    }
+    const unsigned wmin = __reduce_min_sync(FULL, best);
+    ++n_win;
+    if (wmin == kNone) {
+      it += (unsigned)wlen;
+      mb += wlen;
+      if (mb >= M) mb -= M;
+      decode_pair(N, mb, cr, cs);
+      blk_it += wlen;
+      n_it += (unsigned)wlen;
+      K = min(2 * K, kmax);
+      continue;
+    }
+    const int wl = __ffs(__ballot_sync(FULL, best == wmin)) - 1;
+    const int j = (int)(wmin >> 1);
+    const int rs = __shfl_sync(FULL, brs, wl);
+    const int dlt = __shfl_sync(FULL, bdv, wl);
+    const int r = rs >> 16, s = rs & 0xFFFF;
+    if (wmin & 1u) {  // undecided by the binary32 pre-test: binary64
+      int dec = 0;
+      if (lane == 0) {
+        ++n_exact;
+        dec = exact_accept(seed, stream, T0, P, dlt, it + (unsigned)j, &c64[kC64Near]);
+      }
+      dec = __shfl_sync(FULL, dec, 0);
+      if (!dec) {
+        it += (unsigned)j + 1;
+        mb += j + 1;
+        if (mb >= M) mb -= M;
+        cr = r;
+        cs = s;
+        next_pair(N, cr, cs);
+        blk_it += j + 1;
+        n_it += (unsigned)j + 1;
+        continue;
+      }
+    }
+    if (r < 0 || r >= s || s >= N) {
+      err = 1;
+      break;
+    }
+    // ---- accept the swap (r, s) ----
+    if (j < K / 8) K = max(min(32, kmax), K / 2);
+    it += (unsigned)j + 1;
+    mb += j + 1;
+    if (mb >= M) mb -= M;
+    cr = r;
+    cs = s;
+    next_pair(N, cr, cs);
+    blk_it += j + 1;
+    ++blk_acc;
+    n_it += (unsigned)j + 1;
+    ++n_acc;
+    d_cost += dlt;
+    // B' rows and columns r,s (Eq. 3); d_k += (A_rk - A_sk)(B'_sk - B'_rk);
+    // d_r, d_s of the new p.  A lane takes four consecutive k: one 32-bit word
+    // of rows r,s of A and B' and one int4 of d; rows r and s of B' trade their
+    // words except the bytes of columns r,s, columns r,s are stored by byte.
+    int dr_part = 0, ds_part = 0;
+    for (int k0 = 4 * lane; k0 < N; k0 += 128) {
+      const int ar = *reinterpret_cast<const int *>(s_A + r * S + k0);
+      const int as = *reinterpret_cast<const int *>(s_A + s * S + k0);
+      const int br = *reinterpret_cast<const int *>(s_B + r * S + k0);
+      const int bs = *reinterpret_cast<const int *>(s_B + s * S + k0);
+      int4 dq = *reinterpret_cast<const int4 *>(s_d + k0);
+      int dd[4] = {dq.x, dq.y, dq.z, dq.w};
+      unsigned keep = 0;  // bytes of columns r and s: they stay
+      if (r >= k0 && r < k0 + 4) keep |= 0xFFu << (8 * (r - k0));
+      if (s >= k0 && s < k0 + 4) keep |= 0xFFu << (8 * (s - k0));
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = k0 + i;
+        if (k >= N) break;
+        const int Ark = s8_of(ar, i), Ask = s8_of(as, i);
+        const int Brk = s8_of(br, i), Bsk = s8_of(bs, i);
+        if (k != r && k != s) {
+          dd[i] += (Ark - Ask) * (Bsk - Brk);
+          s_B[k * S + r] = (int8_t)Bsk;
+          s_B[k * S + s] = (int8_t)Brk;
+          dr_part += Ark * Bsk;
+          ds_part += Ask * Brk;
+        } else if (k == s) {
+          dr_part += Ark * Brk;  // A_rs B'_rs
+        } else {
+          ds_part += Ask * Bsk;  // A_sr B'_sr
+        }
+      }
+      *reinterpret_cast<int *>(s_B + r * S + k0) =
+          (int)(((unsigned)bs & ~keep) | ((unsigned)br & keep));
+      *reinterpret_cast<int *>(s_B + s * S + k0) =
+          (int)(((unsigned)br & ~keep) | ((unsigned)bs & keep));
+      *reinterpret_cast<int4 *>(s_d + k0) = make_int4(dd[0], dd[1], dd[2], dd[3]);
+    }
+    const int dr = __reduce_add_sync(FULL, dr_part), ds = __reduce_add_sync(FULL, ds_part);
+    __syncwarp();
+    if (lane == 0) {
+      s_d[r] = dr;
+      s_d[s] = ds;
+      const int t = s_p[r];
+      s_p[r] = s_p[s];
+      s_p[s] = t;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    pos->it_lo = (unsigned)it;
+    pos->it_hi = (unsigned)(it >> 32);
+    pos->mb = mb;
+    pos->cr = cr;
+    pos->cs = cs;
+    pos->blk_it = blk_it;
+    pos->blk_acc = blk_acc;
+    pos->err = err;
+    c64[kC64Accepts] += n_acc;
+    c64[kC64Cost] += (unsigned long long)d_cost;
+    c64[kC64Windows] += n_win;
+    c64[kC64Exact] += n_exact;
+    c64[kC64DirIt] += n_it;
+    c64[kC64WarpIt] += n_it;
+    c64[kC64DirAcc] += n_acc;
+  }
+  __syncwarp();
+}
+
+// Mode decisions at the end of a block of kHybBlock iterations (every thread
+// alike): Delta mode below g.hyb_lo, direct mode above 4 g.hyb_lo once in
+// Delta mode, and within direct mode one warp alone from g.warp_lo up.
+__device__ __forceinline__ void t1_block_end(const ChainDev &g, int &mode, bool &rebuild,
+                                             int &warp_mode, int &blk_it, int &blk_acc) {
+  if (blk_it < kHybBlock) return;
+  if (mode == 1 && (float)blk_acc < g.hyb_lo * (float)blk_it) {
+    mode = 0;  // few accepts: maintain Delta from here on
+    rebuild = true;
+  } else if (mode == 0 && g.hyb_lo > 0.0f && (float)blk_acc > 4.0f * g.hyb_lo * (float)blk_it) {
+    mode = 1;  // many accepts again: evaluate proposals directly
+  }
+  warp_mode = (mode == 1 && g.warp_lo > 0.0f && (float)blk_acc >= g.warp_lo * (float)blk_it);
+  blk_it = blk_acc = 0;
+}
+
 // One chain, run by the whole CTA from its state in global memory to iteration
 // it_end and written back.  `smem` holds at least t1_layout(N, S).bytes.
 //
@@ -327,6 +585,7 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
     c64[kC64Windows] = 0;
     c64[kC64DirIt] = 0;
     c64[kC64DirAcc] = 0;
+    c64[kC64WarpIt] = 0;
   }
   unsigned long long it = g.st->it;
   int err = 0;
@@ -341,6 +600,7 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
   int tab_len = 0;                // entries of s_tt that are valid
   int mode = (g.hyb_lo > 0.0f) ? g.st->mode : 0;
   int blk_it = 0, blk_acc = 0;    // iterations and accepts of the current block
+  int warp_mode = (mode == 1 && g.warp_lo > 0.0f);  // direct mode by one warp alone
   bool rebuild = false;           // Delta registers to be recomputed
   // Direct mode: d of the last swap's r and s, taken from the reduction while
   // s_d[r], s_d[s] are being written (one barrier fewer per accepted swap).
@@ -440,6 +700,37 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
     }
     rebuild = false;
     if (last) break;
+
+    if (mode == 1 && warp_mode) {
+      // ================= warp-only direct mode, to the block's end =================
+      WarpPos *pos = reinterpret_cast<WarpPos *>(s_ctl + kT1Pos);
+      if (tid == 0) {
+        pos->it_lo = (unsigned)it;
+        pos->it_hi = (unsigned)(it >> 32);
+        pos->mb = mb;
+        pos->cr = cr;
+        pos->cs = cs;
+        pos->blk_it = blk_it;
+        pos->blk_acc = blk_acc;
+        pos->err = 0;
+      }
+      if (warp == 0)
+        t1_warp_direct(N, S, M, g.seed, g.stream, g.T0, g.P, g.T0f, g.log2a_f, g.mrel, it_end,
+                       s_A, s_B, s_d, s_p, c64, pos);
+      __syncthreads();
+      it = ((unsigned long long)pos->it_hi << 32) | pos->it_lo;
+      mb = pos->mb;
+      cr = pos->cr;
+      cs = pos->cs;
+      blk_it = pos->blk_it;
+      blk_acc = pos->blk_acc;
+      err = pos->err;
+      __syncthreads();  // every thread has read the position before it is reused
+      tab_len = 0;      // the prepared thresholds are for an older position
+      ov_r = ov_s = -1;
+      t1_block_end(g, mode, rebuild, warp_mode, blk_it, blk_acc);
+      continue;
+    }
 
     // ================= scan one window =================
     // Window = iterations it .. it + wlen - 1, wlen <= M, so the proposal at
@@ -667,13 +958,7 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
       it += (unsigned)wlen;
       K = min(K * 2, mode == 1 ? min(M, 4 * per_pass) : M);
       blk_it += wlen;
-      if (blk_it >= 16384) {
-        if (mode == 1 && (float)blk_acc < g.hyb_lo * (float)blk_it) {
-          mode = 0;  // few accepts: maintain Delta from here on
-          rebuild = true;
-        }
-        blk_it = blk_acc = 0;
-      }
+      t1_block_end(g, mode, rebuild, warp_mode, blk_it, blk_acc);
       continue;
     }
     const int j = (int)(code >> 6);
@@ -897,16 +1182,7 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
         s_d[s] = ds;
       }
     }
-    if (blk_it >= 16384) {
-      if (mode == 1 && (float)blk_acc < g.hyb_lo * (float)blk_it) {
-        mode = 0;  // few accepts: maintain Delta from here on
-        rebuild = true;
-      } else if (mode == 0 && g.hyb_lo > 0.0f &&
-                 (float)blk_acc > 4.0f * g.hyb_lo * (float)blk_it) {
-        mode = 1;  // many accepts again: evaluate proposals directly
-      }
-      blk_it = blk_acc = 0;
-    }
+    t1_block_end(g, mode, rebuild, warp_mode, blk_it, blk_acc);
   }
 
   // ---- state back to global memory ----
@@ -951,6 +1227,7 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
     g.st->windows += c64[kC64Windows];
     g.st->direct_iters += c64[kC64DirIt];
     g.st->direct_accepts += c64[kC64DirAcc];
+    g.st->warp_iters += c64[kC64WarpIt];
     g.st->mode = mode;
     if (err) g.st->error = err;
   }

@@ -21,8 +21,8 @@
 //           the CTAs that own them (DSMEM) into local copies, and a_k, b_k,
 //           d_k, d_r, d_s formed from them                     -> CTA barrier
 //   finish  rows r,s of this slice from dot products over local shared memory
-//           plus O(1) corrections for the swap, posted into every CTA (DSMEM);
-//           O(1) update of the register cells                 -> cluster barrier
+//           plus O(1) corrections for the swap, posted into every CTA (DSMEM,
+//           16-byte stores); O(1) update of the TMEM cells    -> cluster barrier
 // and at the top of the next scan each CTA swaps columns r,s of its B' rows (and
 // rewrites rows r,s if it owns them) and copies the recomputed rows into its
 // registers.  All control decisions are computed identically in every CTA from
@@ -73,14 +73,46 @@ struct T2Layout {
 // of 16 bytes, <= kT2MaxS).
 __host__ __device__ inline T2Layout t2_layout(int N, int S, int C) {
   T2Layout L;
-  L.NV = (N + C - 1) / C;
+  L.NV = (((N + C - 1) / C) + 3) & ~3;  // a multiple of 4: rows are posted in fours
   L.bytes = kT2OffSlice + 2 * L.NV * S;
   return L;
 }
 
-// Byte i (0..3) of a packed word of int8 values, sign-extended.
-__device__ __forceinline__ int s8_of(int w, int i) {
-  return static_cast<int8_t>(static_cast<unsigned>(w) >> (8 * i));
+// Sums of 16 values over the 32 lanes of a warp in 16 shuffles: lane l returns
+// the total of v[((l >> 3) & 3) * 4 + ((l >> 1) & 3)] (lanes l and l ^ 1 alike).
+// v is consumed.
+__device__ __forceinline__ int reduce_scatter16(int (&v)[16], int lane) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool hi = lane & 16;
+    const int send = hi ? v[i] : v[i + 8], keep = hi ? v[i + 8] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool hi = lane & 8;
+    const int send = hi ? v[i] : v[i + 4], keep = hi ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = lane & 4;
+    const int send = hi ? v[i] : v[i + 2], keep = hi ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
+  }
+  {
+    const bool hi = lane & 2;
+    const int send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 2);
+  }
+  return v[0] + __shfl_xor_sync(0xFFFFFFFFu, v[0], 1);
+}
+
+__device__ __forceinline__ int dot16(int4 x, int4 y, int acc) {
+  acc = __dp4a(x.x, y.x, acc);
+  acc = __dp4a(x.y, y.y, acc);
+  acc = __dp4a(x.z, y.z, acc);
+  return __dp4a(x.w, y.w, acc);
 }
 
 // One chain on the calling cluster.  Every CTA of the cluster must call it with
@@ -173,11 +205,7 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       }
     tmem_st16(tb + 16 * q, Dq);
   }
-  // dot products: tpv consecutive lanes per slice row, lpt rows per warp
-  const int tpv = g.tpv, lpt = 32 / tpv;
-  const int v_l = lane / tpv, t_sl = lane - v_l * tpv;
-  const int vslots = (nthreads >> 5) * lpt;
-  const int NC = S >> 4;
+  const int NC = S >> 4;  // 16-byte chunks of a row
 
   unsigned long long it = g.st->it;
   int err = 0;
@@ -210,23 +238,24 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
         for (int k = tid; k < N; k += nthreads)
           row[k] = (k == r) ? o_r[s] : (k == s ? o_r[r] : o_r[k]);
       }
-      // ---- recomputed rows/columns r,s -> the TMEM cells (warp-collective) ----
+      // ---- recomputed rows/columns r,s -> the TMEM cells (warp-collective),
+      //      8 rows at a time ----
       const bool col_hit = has_tile && ((r >= v0 && r < v0 + 4) || (s >= v0 && s < v0 + 4));
 #pragma unroll 1
-      for (int q = 0; q < R / 4; ++q) {
-        const int uq = u0 + 4 * q;
-        const bool row_hit = has_tile && ((r >= uq && r < uq + 4) || (s >= uq && s < uq + 4));
+      for (int h = 0; h < R / 8; ++h) {
+        const int uh = u0 + 8 * h;
+        const bool row_hit = has_tile && ((r >= uh && r < uh + 8) || (s >= uh && s < uh + 8));
         if (!__any_sync(0xFFFFFFFFu, row_hit || col_hit)) continue;
-        int Dq[16];
-        tmem_ld16(tb + 16 * q, Dq);
+        int Dh[32];
+        tmem_ld32(tb + 32 * h, Dh);
         if (row_hit) {
 #pragma unroll
-          for (int ii = 0; ii < 4; ++ii) {
-            const int u = uq + ii;
+          for (int ii = 0; ii < 8; ++ii) {
+            const int u = uh + ii;
             if (u == r || u == s) {
               const int *src = (u == r) ? s_nr : s_ns;
 #pragma unroll
-              for (int c = 0; c < 4; ++c) Dq[4 * ii + c] = src[v0 + c];
+              for (int c = 0; c < 4; ++c) Dh[4 * ii + c] = src[v0 + c];
             }
           }
         }
@@ -237,11 +266,11 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
             if (v == r || v == s) {
               const int *src = (v == r) ? s_nr : s_ns;
 #pragma unroll
-              for (int ii = 0; ii < 4; ++ii) Dq[4 * ii + c] = src[uq + ii];
+              for (int ii = 0; ii < 8; ++ii) Dh[4 * ii + c] = src[uh + ii];
             }
           }
         }
-        tmem_st16(tb + 16 * q, Dq);
+        tmem_st32(tb + 32 * h, Dh);
       }
     }
     pend_r = -1;
@@ -452,8 +481,11 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     // ---- rows r,s of this slice under the new p, from dot products on B'
     //      before the swap plus the O(1) terms the swap changes:
     //      <A_r, B'new_v> = <A_r, B_v> + A_rs (B_vr - B_vs),
-    //      <A_v, B'new_r> = <A_v, B_s> + (A_vs - A_vr) B_rs, and symmetrically;
-    //      posted into every CTA ----
+    //      <A_v, B'new_r> = <A_v, B_s> + (A_vs - A_vr) B_rs, and symmetrically.
+    //      Warp w takes slice rows vq .. vq+3 (vq = sv_lo + 4w, + 4 warps ...),
+    //      its lanes the 16-byte chunks, so rows r,s of A and B' are read once
+    //      per four slice rows; the four results are posted into every CTA as
+    //      one 16-byte store per row of values ----
     {
       const int dr = (int)s_ctl[kT1Dr], ds = (int)s_ctl[kT1Ds];
       const int Ars = a_r[s], Brs = o_r[s];
@@ -461,47 +493,57 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       const int4 *As4 = reinterpret_cast<const int4 *>(a_s);
       const int4 *Br4 = reinterpret_cast<const int4 *>(o_r);
       const int4 *Bs4 = reinterpret_cast<const int4 *>(o_s);
-      for (int vb = 0; vb < sv_hi - sv_lo; vb += vslots) {
-        const int v = sv_lo + vb + warp * lpt + v_l;
-        int g1 = 0, g2 = 0, g3 = 0, g4 = 0;
+      const int nw = nthreads >> 5;
+      for (int vq = sv_lo + 4 * warp; vq < sv_hi; vq += 4 * nw) {
+        const int nk = min(4, sv_hi - vq);
+        int gk[16];  // [k][<A_r,B_v>, <A_s,B_v>, <A_v,B_s>, <A_v,B_r>], v = vq + k
+#pragma unroll
+        for (int i = 0; i < 16; ++i) gk[i] = 0;
+        for (int c = lane; c < NC; c += 32) {
+          const int4 ar = Ar4[c], as = As4[c], br = Br4[c], bs = Bs4[c];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (k < nk) {
+              const int row = (vq + k - sv_lo) * S;
+              const int4 bv = reinterpret_cast<const int4 *>(s_B + row)[c];
+              const int4 av = reinterpret_cast<const int4 *>(s_A + row)[c];
+              gk[4 * k + 0] = dot16(ar, bv, gk[4 * k + 0]);
+              gk[4 * k + 1] = dot16(as, bv, gk[4 * k + 1]);
+              gk[4 * k + 2] = dot16(av, bs, gk[4 * k + 2]);
+              gk[4 * k + 3] = dot16(av, br, gk[4 * k + 3]);
+            }
+          }
+        }
+        const int tot = reduce_scatter16(gk, lane);
+        const int kb = lane & ~7;  // lanes kb .. kb+7 hold row k = lane >> 3
+        const int G1 = __shfl_sync(0xFFFFFFFFu, tot, kb);
+        const int G2 = __shfl_sync(0xFFFFFFFFu, tot, kb + 2);
+        const int G3 = __shfl_sync(0xFFFFFFFFu, tot, kb + 4);
+        const int G4 = __shfl_sync(0xFFFFFFFFu, tot, kb + 6);
+        const int v = vq + (lane >> 3);
+        int nr = 0, ns = 0;
         if (v < sv_hi) {
-          const int4 *Av4 = reinterpret_cast<const int4 *>(s_A + (v - sv_lo) * S);
-          const int4 *Bv4 = reinterpret_cast<const int4 *>(s_B + (v - sv_lo) * S);
-          for (int c = t_sl; c < NC; c += tpv) {
-            const int4 bv = Bv4[c];
-            int4 x = Ar4[c];
-            g1 = __dp4a(x.x, bv.x, g1); g1 = __dp4a(x.y, bv.y, g1);
-            g1 = __dp4a(x.z, bv.z, g1); g1 = __dp4a(x.w, bv.w, g1);
-            x = As4[c];
-            g2 = __dp4a(x.x, bv.x, g2); g2 = __dp4a(x.y, bv.y, g2);
-            g2 = __dp4a(x.z, bv.z, g2); g2 = __dp4a(x.w, bv.w, g2);
-            const int4 av = Av4[c];
-            x = Bs4[c];
-            g3 = __dp4a(av.x, x.x, g3); g3 = __dp4a(av.y, x.y, g3);
-            g3 = __dp4a(av.z, x.z, g3); g3 = __dp4a(av.w, x.w, g3);
-            x = Br4[c];
-            g4 = __dp4a(av.x, x.x, g4); g4 = __dp4a(av.y, x.y, g4);
-            g4 = __dp4a(av.z, x.z, g4); g4 = __dp4a(av.w, x.w, g4);
+          if (v == s) {
+            nr = -dlt;  // Delta_rs of the new p
+          } else if (v == r) {
+            ns = -dlt;
+          } else {
+            const int Avr = a_r[v], Avs = a_s[v];
+            const int Bvr = o_r[v], Bvs = o_s[v];
+            const int dv = s_d[v];
+            nr = 2 * (G1 + Ars * (Bvr - Bvs) + G3 + (Avs - Avr) * Brs - dr - dv +
+                      2 * Avr * Bvs);
+            ns = 2 * (G2 - Ars * (Bvr - Bvs) + G4 - (Avs - Avr) * Brs - ds - dv +
+                      2 * Avs * Bvr);
           }
         }
-        for (int o = 1; o < tpv; o <<= 1) {
-          g1 += __shfl_xor_sync(0xFFFFFFFFu, g1, o);
-          g2 += __shfl_xor_sync(0xFFFFFFFFu, g2, o);
-          g3 += __shfl_xor_sync(0xFFFFFFFFu, g3, o);
-          g4 += __shfl_xor_sync(0xFFFFFFFFu, g4, o);
-        }
-        if (v < sv_hi && v != r && v != s) {
-          const int Avr = a_r[v], Avs = a_s[v];
-          const int Bvr = o_r[v], Bvs = o_s[v];
-          const int dv = s_d[v];
-          const int nr = 2 * (g1 + Ars * (Bvr - Bvs) + g3 + (Avs - Avr) * Brs -
-                              dr - dv + 2 * Avr * Bvs);
-          const int ns = 2 * (g2 - Ars * (Bvr - Bvs) + g4 - (Avs - Avr) * Brs -
-                              ds - dv + 2 * Avs * Bvr);
-          for (int q = t_sl; q < C; q += tpv) {
-            cluster.map_shared_rank(s_nr, q)[v] = nr;
-            cluster.map_shared_rank(s_ns, q)[v] = ns;
-          }
+        const int4 nq = make_int4(__shfl_sync(0xFFFFFFFFu, nr, 0), __shfl_sync(0xFFFFFFFFu, nr, 8),
+                                  __shfl_sync(0xFFFFFFFFu, nr, 16), __shfl_sync(0xFFFFFFFFu, nr, 24));
+        const int4 sq = make_int4(__shfl_sync(0xFFFFFFFFu, ns, 0), __shfl_sync(0xFFFFFFFFu, ns, 8),
+                                  __shfl_sync(0xFFFFFFFFu, ns, 16), __shfl_sync(0xFFFFFFFFu, ns, 24));
+        if (lane < C) {  // vq is a multiple of 4: 16-byte aligned
+          *reinterpret_cast<int4 *>(cluster.map_shared_rank(s_nr, lane) + vq) = nq;
+          *reinterpret_cast<int4 *>(cluster.map_shared_rank(s_ns, lane) + vq) = sq;
         }
       }
     }
@@ -525,28 +567,26 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
         }
       }
     }
-    // ---- O(1) update of the TMEM cells (warp-collective) ----
+    // ---- O(1) update of the TMEM cells (warp-collective), 8 rows at a time ----
     if (__any_sync(0xFFFFFFFFu, has_tile)) {
       const int4 av = *reinterpret_cast<const int4 *>(s_a + v0);
       const int4 bv = *reinterpret_cast<const int4 *>(s_b + v0);
 #pragma unroll 1
-      for (int q = 0; q < R / 4; ++q) {
-        int Dq[16];
-        tmem_ld16(tb + 16 * q, Dq);
+      for (int h = 0; h < R / 8; ++h) {
+        int Dh[32];
+        tmem_ld32(tb + 32 * h, Dh);
 #pragma unroll
-        for (int ii = 0; ii < 4; ++ii) {
-          const int au = s_a[u0 + 4 * q + ii], bu_ = s_b[u0 + 4 * q + ii];
-          Dq[4 * ii + 0] += (au - av.x) * (bv.x - bu_);
-          Dq[4 * ii + 1] += (au - av.y) * (bv.y - bu_);
-          Dq[4 * ii + 2] += (au - av.z) * (bv.z - bu_);
-          Dq[4 * ii + 3] += (au - av.w) * (bv.w - bu_);
+        for (int ii = 0; ii < 8; ++ii) {
+          const int au = s_a[u0 + 8 * h + ii], bu_ = s_b[u0 + 8 * h + ii];
+          Dh[4 * ii + 0] += (au - av.x) * (bv.x - bu_);
+          Dh[4 * ii + 1] += (au - av.y) * (bv.y - bu_);
+          Dh[4 * ii + 2] += (au - av.z) * (bv.z - bu_);
+          Dh[4 * ii + 3] += (au - av.w) * (bv.w - bu_);
         }
-        tmem_st16(tb + 16 * q, Dq);
+        tmem_st32(tb + 32 * h, Dh);
       }
     }
     if (tid == 0) {
-      s_nr[s] = -dlt;
-      s_ns[r] = -dlt;
       s_d[r] = (int)s_ctl[kT1Dr];
       s_d[s] = (int)s_ctl[kT1Ds];
     }

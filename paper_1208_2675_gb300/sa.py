@@ -43,7 +43,7 @@ class qap_sa_info(ctypes.Structure):
                 ("T0", ctypes.c_double), ("Tf", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("total_iters", ctypes.c_uint64),
                 ("smem_bytes", ctypes.c_uint64), ("direct_iters", ctypes.c_uint64),
-                ("direct_accepts", ctypes.c_uint64)]
+                ("direct_accepts", ctypes.c_uint64), ("warp_iters", ctypes.c_uint64)]
 
 
 class qap_problem(ctypes.Structure):

@@ -296,3 +296,32 @@ def test_direct_and_delta_modes_give_the_same_trajectory(rate, monkeypatch):
                                      splits=[150000, 250000])
     assert os_["accepts"] > 1000
     assert_same(gs, os_, gd, od)
+
+
+@pytest.mark.parametrize("N,warp_rate", [(64, "1e-9"), (64, "0"), (100, "1e-9"), (150, "1e-9"),
+                                         (230, "1e-9"), (12, "1e-9"), (2, "1e-9"), (3, "1e-9")])
+def test_warp_only_direct_mode_gives_the_same_trajectory(N, warp_rate, monkeypatch):
+    """One warp evaluating proposals and applying swaps alone (windows of 32 to
+    128, no block barrier) against the oracle; warp_rate 1e-9: whenever the
+    chain is in direct mode, 0: never.  Runs split across launches."""
+    monkeypatch.setenv("QAPSA_HYBRID_RATE", "5e-4")
+    monkeypatch.setenv("QAPSA_WARP_RATE", warp_rate)
+    A, B, p0 = instances.taixxa_like(N, 43)
+    I = 300000
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=I, seed=43,
+                                     splits=[1, 99999, I - 100000])
+    assert_same(gs, os_, gd, od)
+    if warp_rate == "0":
+        assert gs["info"]["warp_iters"] == 0
+    elif N > 3:
+        assert gs["info"]["warp_iters"] > 10000
+
+
+def test_warp_mode_default_threshold_runs_and_matches():
+    """The default thresholds on the N = 100 workload's schedule: the warp-only
+    mode carries the hot start, the CTA modes the rest, one trajectory."""
+    A, B, p0 = instances.taixxa_like(100, 1)
+    gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=10 ** 8, seed=1,
+                                     oracle_iters=300000)
+    assert_same(gs, os_, gd, od)
+    assert gs["info"]["warp_iters"] > 100000
