@@ -251,7 +251,15 @@ __device__ __forceinline__ int dot16x(int4 x, int4 y, int acc) {
 // position comes from and goes back to *pos; returns at it_end, at the end of
 // the current block of kHybBlock iterations, or on an inconsistency.  Counters
 // go to c64 (lane 0).
-__device__ __noinline__ void t1_warp_direct(int N, int S, int M, unsigned long long seed,
+//
+// LPP lanes evaluate one proposal (the dot products split over them), so a pass
+// takes 32 / LPP proposals.  The loop is a function of its own, not inlined,
+// and a kernel calls one instantiation only: one warp runs it alone for
+// thousands of iterations and it must stay small in the instruction cache
+// (with all three instantiations reachable from one kernel the warp mode ran
+// three times slower).
+template <int LPP>
+__device__ __noinline__ void t1_warp_run(int N, int S, int M, unsigned long long seed,
                                             unsigned stream, double T0, const double *P,
                                             float T0f, float log2a_f, float mrel,
                                             unsigned long long it_end,
@@ -270,6 +278,9 @@ __device__ __noinline__ void t1_warp_direct(int N, int S, int M, unsigned long l
   long long d_cost = 0;
   const int kmax = min(M, kWarpMaxK);
   int K = min(32, kmax);
+  constexpr int lpp = LPP;  // lanes per proposal
+  constexpr int ppp = 32 / LPP;
+  const int sub = lane & (LPP - 1);
   // Rolling table of Eq. (2) pre-test intervals in registers: lane l holds
   // those of Philox block q0 + l (iterations 4 (q0 + l) .. + 3), computed as the
   // prepared table computes them; a proposal fetches its own by shuffles.
@@ -279,10 +290,10 @@ __device__ __noinline__ void t1_warp_direct(int N, int S, int M, unsigned long l
     const int wlen = (int)min((unsigned long long)K, it_end - it);
     unsigned best = kNone;
     int brs = 0, bdv = 0;
-    for (int j0 = 0; j0 < wlen; j0 += 32) {
+    for (int j0 = 0; j0 < wlen; j0 += ppp) {
       {
         const unsigned long long qa = (it + (unsigned)j0) >> 2;
-        if (qa < q0 || ((it + (unsigned)j0 + 31u) >> 2) >= q0 + 32) {  // refill
+        if (qa < q0 || ((it + (unsigned)(j0 + ppp - 1)) >> 2) >= q0 + 32) {  // refill
           q0 = qa;
           const unsigned long long q = q0 + (unsigned)lane;
           const uint4 x = rng_block(seed, stream, q);
@@ -293,7 +304,7 @@ __device__ __noinline__ void t1_warp_direct(int N, int S, int M, unsigned long l
           tb3 = accept_interval(mrel, Tq * exp2f(3.0f * log2a_f), x.w);
         }
       }
-      const int j = j0 + lane;
+      const int j = j0 + lane / lpp;
       float2 b;
       {
         const unsigned long long itc = it + (unsigned)j;
@@ -305,8 +316,8 @@ __device__ __noinline__ void t1_warp_direct(int N, int S, int M, unsigned long l
         b.x = w == 0 ? x0 : (w == 1 ? x1 : (w == 2 ? x2 : x3));
         b.y = w == 0 ? y0 : (w == 1 ? y1 : (w == 2 ? y2 : y3));
       }
+      int r = cr, s = cs + j, g1 = 0, g2 = 0;
       if (j < wlen) {
-        int r = cr, s = cs + j;
         while (s >= N) {  // on into the next rows of the cyclic order
           const int o = s - N;
           if (++r >= N - 1) r = 0;
@@ -316,12 +327,17 @@ __device__ __noinline__ void t1_warp_direct(int N, int S, int M, unsigned long l
         const int4 *As4 = reinterpret_cast<const int4 *>(s_A + s * S);
         const int4 *Br4 = reinterpret_cast<const int4 *>(s_B + r * S);
         const int4 *Bs4 = reinterpret_cast<const int4 *>(s_B + s * S);
-        int g1 = 0, g2 = 0;
 #pragma unroll 4
-        for (int c = 0; c < NC; ++c) {
+        for (int c = sub; c < NC; c += lpp) {
           g1 = dot16x(Ar4[c], Bs4[c], g1);
           g2 = dot16x(As4[c], Br4[c], g2);
         }
+      }
+      for (int o = 1; o < lpp; o <<= 1) {
+        g1 += __shfl_xor_sync(FULL, g1, o);
+        g2 += __shfl_xor_sync(FULL, g2, o);
+      }
+      if (j < wlen && sub == 0) {
         const int dv = 2 * (g1 + g2 - s_d[r] - s_d[s] +
                             2 * (int)s_A[r * S + s] * (int)s_B[r * S + s]);
         const float df = (float)dv;
@@ -391,14 +407,17 @@ __device__ __noinline__ void t1_warp_direct(int N, int S, int M, unsigned long l
     // B' rows and columns r,s (Eq. 3); d_k += (A_rk - A_sk)(B'_sk - B'_rk);
     // d_r, d_s of the new p.  A lane takes four consecutive k: one 32-bit word
     // of rows r,s of A and B' and one int4 of d; rows r and s of B' trade their
-    // words except the bytes of columns r,s, columns r,s are stored by byte.
+    // words except the bytes of columns r,s; columns r,s are stored by byte.
     int dr_part = 0, ds_part = 0;
-    for (int k0 = 4 * lane; k0 < N; k0 += 128) {
-      const int ar = *reinterpret_cast<const int *>(s_A + r * S + k0);
-      const int as = *reinterpret_cast<const int *>(s_A + s * S + k0);
-      const int br = *reinterpret_cast<const int *>(s_B + r * S + k0);
-      const int bs = *reinterpret_cast<const int *>(s_B + s * S + k0);
-      int4 dq = *reinterpret_cast<const int4 *>(s_d + k0);
+    for (int kb = 0; kb < N; kb += 128) {
+      const int k0 = kb + 4 * lane;
+      const bool live = k0 < N;
+      const int kr = live ? k0 : 0;
+      const int ar = *reinterpret_cast<const int *>(s_A + r * S + kr);
+      const int as = *reinterpret_cast<const int *>(s_A + s * S + kr);
+      const int br = *reinterpret_cast<const int *>(s_B + r * S + kr);
+      const int bs = *reinterpret_cast<const int *>(s_B + s * S + kr);
+      int4 dq = *reinterpret_cast<const int4 *>(s_d + kr);
       int dd[4] = {dq.x, dq.y, dq.z, dq.w};
       unsigned keep = 0;  // bytes of columns r and s: they stay
       if (r >= k0 && r < k0 + 4) keep |= 0xFFu << (8 * (r - k0));
@@ -406,7 +425,7 @@ __device__ __noinline__ void t1_warp_direct(int N, int S, int M, unsigned long l
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int k = k0 + i;
-        if (k >= N) break;
+        if (!live || k >= N) break;
         const int Ark = s8_of(ar, i), Ask = s8_of(as, i);
         const int Brk = s8_of(br, i), Bsk = s8_of(bs, i);
         if (k != r && k != s) {
@@ -421,11 +440,13 @@ __device__ __noinline__ void t1_warp_direct(int N, int S, int M, unsigned long l
           ds_part += Ask * Bsk;  // A_sr B'_sr
         }
       }
-      *reinterpret_cast<int *>(s_B + r * S + k0) =
-          (int)(((unsigned)bs & ~keep) | ((unsigned)br & keep));
-      *reinterpret_cast<int *>(s_B + s * S + k0) =
-          (int)(((unsigned)br & ~keep) | ((unsigned)bs & keep));
-      *reinterpret_cast<int4 *>(s_d + k0) = make_int4(dd[0], dd[1], dd[2], dd[3]);
+      if (live) {
+        *reinterpret_cast<int *>(s_B + r * S + k0) =
+            (int)(((unsigned)bs & ~keep) | ((unsigned)br & keep));
+        *reinterpret_cast<int *>(s_B + s * S + k0) =
+            (int)(((unsigned)br & ~keep) | ((unsigned)bs & keep));
+        *reinterpret_cast<int4 *>(s_d + k0) = make_int4(dd[0], dd[1], dd[2], dd[3]);
+      }
     }
     const int dr = __reduce_add_sync(FULL, dr_part), ds = __reduce_add_sync(FULL, ds_part);
     __syncwarp();
@@ -491,7 +512,8 @@ __device__ __forceinline__ void t1_block_end(const ChainDev &g, int &mode, bool 
 //
 // TM: the tiles live in TMEM at address tb (this thread's lane, 4R columns)
 // instead of registers; every TMEM access below is reached by whole warps.
-template <int R, bool TM>
+// WLPP: lanes per proposal of the warp-only direct mode.
+template <int R, bool TM, int WLPP>
 __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
                                              unsigned long long it_end,
                                              unsigned char *smem, unsigned tb) {
@@ -715,8 +737,8 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
         pos->err = 0;
       }
       if (warp == 0)
-        t1_warp_direct(N, S, M, g.seed, g.stream, g.T0, g.P, g.T0f, g.log2a_f, g.mrel, it_end,
-                       s_A, s_B, s_d, s_p, c64, pos);
+        t1_warp_run<WLPP>(N, S, M, g.seed, g.stream, g.T0, g.P, g.T0f, g.log2a_f, g.mrel,
+                          it_end, s_A, s_B, s_d, s_p, c64, pos);
       __syncthreads();
       it = ((unsigned long long)pos->it_hi << 32) | pos->it_lo;
       mb = pos->mb;
@@ -1237,13 +1259,14 @@ template <int BOUND>
 __global__ void __launch_bounds__(BOUND, 1)
     sa_tier1_kernel(ChainDev g, unsigned long long it_end) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if constexpr (BOUND > kT1SmallThreads) {  // 96 registers a thread: tiles in TMEM
+  if constexpr (BOUND > kT1SmallThreads) {  // 96 registers a thread: tiles in TMEM;
+                                            // long rows: 4 lanes per proposal
     __shared__ unsigned s_tmem;
     const unsigned tb = tile_tmem_acquire(&s_tmem, 4 * kT1R);
-    t1_run_chain<kT1R, true>(g, it_end, smem, tb);
+    t1_run_chain<kT1R, true, 4>(g, it_end, smem, tb);
     tile_tmem_release(&s_tmem);
   } else {
-    t1_run_chain<kT1R, false>(g, it_end, smem, 0u);
+    t1_run_chain<kT1R, false, 1>(g, it_end, smem, 0u);
   }
 }
 
@@ -1277,7 +1300,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     const int k = s_next;
     if (k >= n) break;
     const BatchChain &bc = chains[order[k]];
-    t1_run_chain<kT1R, true>(bc.g, bc.it_end, smem, tb);
+    t1_run_chain<kT1R, true, 1>(bc.g, bc.it_end, smem, tb);
   }
   tile_tmem_release(&s_tmem);
 }

@@ -299,11 +299,14 @@ def test_direct_and_delta_modes_give_the_same_trajectory(rate, monkeypatch):
 
 
 @pytest.mark.parametrize("N,warp_rate", [(64, "1e-9"), (64, "0"), (100, "1e-9"), (150, "1e-9"),
-                                         (230, "1e-9"), (12, "1e-9"), (2, "1e-9"), (3, "1e-9")])
+                                         (230, "1e-9"), (276, "1e-9"), (12, "1e-9"), (2, "1e-9"),
+                                         (3, "1e-9")])
 def test_warp_only_direct_mode_gives_the_same_trajectory(N, warp_rate, monkeypatch):
     """One warp evaluating proposals and applying swaps alone (windows of 32 to
     128, no block barrier) against the oracle; warp_rate 1e-9: whenever the
-    chain is in direct mode, 0: never.  Runs split across launches."""
+    chain is in direct mode, 0: never.  Runs split across launches.  The sizes
+    cover one, two and four lanes per proposal and the 256- and 640-thread
+    kernels."""
     monkeypatch.setenv("QAPSA_HYBRID_RATE", "5e-4")
     monkeypatch.setenv("QAPSA_WARP_RATE", warp_rate)
     A, B, p0 = instances.taixxa_like(N, 43)
