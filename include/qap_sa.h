@@ -147,7 +147,8 @@ typedef struct qap_sa_info {
                              (high acceptance) instead of read from Delta  */
   uint64_t direct_accepts;/* accepted swaps among them (no Delta update)    */
   uint64_t warp_iters;    /* direct iterations run by one warp alone, with no
-                             block barrier (acceptance rate >= 1/256)       */
+                             block barrier (while the acceptance rate is
+                             above 1/512, or 1/64 for N above ~180)        */
 } qap_sa_info;
 QAP_EXPORT int qap_sa_get_info(qap_sa *h, qap_sa_info *out);
 

@@ -451,14 +451,18 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   g.mrel = (float)(2e-5 + 2e-7 * fabs(l2r) + 8.0 * (double)sc->total_iters * 0x1p-53);
   // Acceptance rate below which the one-SM tier maintains Delta (above it,
   // proposals are evaluated directly): where one accepted swap's O(N^2) update
-  // costs as much as evaluating ~2000 proposals directly.  From one accept in
-  // 256 proposals up, one warp evaluates them alone (windows of 32..128, no
-  // block barrier per accepted swap).
+  // costs as much as evaluating ~2000 proposals directly.  Above warp_lo one
+  // warp evaluates them alone (windows of 32..128, no block barrier per
+  // accepted swap): from 1 accept in 512 proposals for the 256-thread kernel
+  // (one lane per proposal), from 1 in 64 for the 640-thread one (four lanes
+  // per proposal, eight proposals a pass).  Both from a sweep of whole runs at
+  // N = 60..276; the modes change the speed only, never the trajectory.
   {
     const char *e = getenv("QAPSA_HYBRID_RATE");
     g.hyb_lo = (h->tier == 1) ? (e ? (float)atof(e) : 5e-4f) : 0.0f;
     const char *ew = getenv("QAPSA_WARP_RATE");
-    g.warp_lo = (h->tier == 1) ? (ew ? (float)atof(ew) : 1.0f / 256.0f) : 0.0f;
+    const float wdef = (h->nthreads <= kT1SmallThreads) ? 1.0f / 512.0f : 1.0f / 64.0f;
+    g.warp_lo = (h->tier == 1) ? (ew ? (float)atof(ew) : wdef) : 0.0f;
   }
   h->layout = t1_layout(N, S);
   h->smem_bytes = h->tier == 1 ? h->layout.bytes : tier2_bytes(N, h->cluster);
