@@ -29,7 +29,15 @@ WORKLOADS = {
     "n100": dict(N=100, I=10 ** 8, seed=1, cpu_div=10,
                  desc="single chain, N=100, A and B symmetric uniform int [0,99], "
                       "zero diagonal, random p0, geometric cooling "
-                      "T0=0.5*mean|Delta0|, Tf=1e-3*T0, I=1e8"),
+                      "T0=0.5*mean|Delta0|, Tf=1e-3*T0, I=1e8",
+                 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of
+                 # sa_tier1_kernel<256> on this instance (2e6 iterations): the chain
+                 # state and the code are read once per launch and everything stays
+                 # on chip, so a launch of any length moves the same bytes
+                 dram_bytes_per_launch=993792,
+                 traffic_basis="ncu capture of one 2e6-iteration launch of the same "
+                               "kernel on this instance; independent of the launch's "
+                               "length (state on chip)"),
     "n256": dict(N=256, I=10 ** 9, seed=1, cpu_div=200,
                  desc="single chain, N=256, A and B symmetric uniform int [0,99], "
                       "zero diagonal, random p0, geometric cooling "
@@ -249,6 +257,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
     achieved = bytes_step / t_kernel / 1e9
     mhz = clk.get("sm_mhz") or 2070.0
     peak = SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6 / 1e9  # one SM
+    traffic = wl.get("dram_bytes_per_launch")
     line = {
         "metric": "sa_iterations_per_sec",
         "value": value,
@@ -276,7 +285,8 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
                 "d2h_bytes_per_step": 4 * N + 8 + 8},
         "gpu_launches": args.steps * (4 + sa_launches),
         "roofline": {"bound": "smem", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "traffic_basis": wl.get("traffic_basis"),
                      "peak_basis": "one SM: 128 B/clk x median SM clock under load "
                                    "(derived; the kernel runs on one CTA)",
                      "frac_of_chip": achieved / (peak * 152)},
