@@ -212,6 +212,8 @@ void preload_kernels() {
     cudaFuncGetAttributes(&a, setup_bprime_kernel);
     cudaFuncGetAttributes(&a, setup_gram_kernel);
     cudaFuncGetAttributes(&a, setup_delta_kernel);
+    cudaFuncGetAttributes(&a, rebuild_delta_kernel);
+    cudaFuncGetAttributes(&a, clear_rebuild_kernel);
     const int smem = device_smem_optin();
     // the limit covers dynamic shared memory only: the kernel's static part
     // comes off the device's opt-in size
@@ -460,6 +462,10 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   {
     const char *e = getenv("QAPSA_HYBRID_RATE");
     g.hyb_lo = (h->tier == 1) ? (e ? (float)atof(e) : 5e-4f) : 0.0f;
+    if (h->tier == 2) {  // the cluster tier: direct mode at high acceptance as well
+      const char *ec = getenv("QAPSA_CLUSTER_HYBRID_RATE");
+      g.hyb_lo = ec ? (float)atof(ec) : 2e-3f;
+    }
     const char *ew = getenv("QAPSA_WARP_RATE");
     const float wdef = (h->nthreads <= kT1SmallThreads) ? 1.0f / 512.0f : 1.0f / 64.0f;
     g.warp_lo = (h->tier == 1) ? (ew ? (float)atof(ew) : wdef) : 0.0f;
@@ -569,8 +575,20 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
     unsigned long long stop = cur + chunk_iters();
     if (stop > end) stop = end;
     if (h->tier == 2) {
-      cudaError_t e2 = launch_tier2(h->dev, stop, h->cluster, h->smem_bytes, h->stream);
-      if (e2 != cudaSuccess) return cuda_fail(e2, "sa_tier2_kernel launch");
+      // With the direct mode enabled a launch may leave Delta in global memory
+      // stale (it ended in direct mode) or stop early to switch to Delta mode:
+      // rebuild Delta if flagged, and launch again to the same end (a no-op if
+      // the first launch got there).  The second launch starts in Delta mode or
+      // at the end, so it never stops early.
+      const int rounds = h->dev.hyb_lo > 0.0f ? 2 : 1;
+      for (int k = 0; k < rounds; ++k) {
+        cudaError_t e2 = launch_tier2(h->dev, stop, h->cluster, h->smem_bytes, h->stream);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "sa_tier2_kernel launch");
+        if (rounds > 1) {
+          rebuild_delta_kernel<<<dim3((h->N + 127) / 128, h->N), 128, 0, h->stream>>>(h->dev);
+          clear_rebuild_kernel<<<1, 1, 0, h->stream>>>(h->st);
+        }
+      }
     } else if (h->nthreads <= kT1SmallThreads) {
       sa_tier1_kernel<kT1SmallThreads>
           <<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
@@ -751,6 +769,13 @@ int qap_batch_create(const qap_problem *probs, int32_t count, qap_batch **out) {
       return rc;
     }
     b->h.push_back(h);
+    if (h->tier == 2) {  // the persistent cluster launch keeps Delta throughout
+      h->dev.hyb_lo = 0.0f;
+      if ((e = cudaMemsetAsync(&h->st->mode, 0, sizeof(int), b->stream)) != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(e, "cudaMemsetAsync");
+      }
+    }
     BatchChain bc{};
     bc.g = h->dev;
     bc.it_end = 0;

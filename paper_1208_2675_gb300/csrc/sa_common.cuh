@@ -33,6 +33,9 @@ struct ChainStatus {
   unsigned long long direct_iters;    // iterations whose proposal was evaluated directly
   unsigned long long direct_accepts;  // accepted swaps among them
   unsigned long long warp_iters;      // direct iterations run by one warp alone
+  int need_rebuild;                   // Delta in global memory is stale (cluster
+                                      // tier after direct mode): rebuild it
+  int pad_;
 };
 
 // Everything one chain's kernels need (passed by value).

@@ -62,7 +62,9 @@ constexpr int kT2OffRowAr = kT2OffVns + 4 * kT2NP;  // row r of A
 constexpr int kT2OffRowAs = kT2OffRowAr + kT2MaxS;  // row s of A
 constexpr int kT2OffRowBr = kT2OffRowAs + kT2MaxS;  // row r of B' before the swap
 constexpr int kT2OffRowBs = kT2OffRowBr + kT2MaxS;  // row s of B' before the swap
-constexpr int kT2OffSlice = kT2OffRowBs + kT2MaxS;  // this CTA's rows of A, then of B'
+constexpr int kT2OffRowWa = kT2OffRowBs + kT2MaxS;  // direct mode: row cr of A
+constexpr int kT2OffRowWb = kT2OffRowWa + kT2MaxS;  // direct mode: row cr of B'
+constexpr int kT2OffSlice = kT2OffRowWb + kT2MaxS;  // this CTA's rows of A, then of B'
 
 struct T2Layout {
   int NV;  // rows of A and B' per CTA
@@ -115,6 +117,28 @@ __device__ __forceinline__ int dot16(int4 x, int4 y, int acc) {
   return __dp4a(x.w, y.w, acc);
 }
 
+// Mode decisions of the cluster tier at the end of a block of kHybBlock
+// iterations (every thread of every CTA alike): to direct mode above
+// 4 g.hyb_lo; back to Delta mode below g.hyb_lo, which ends a launch that
+// started in direct mode (Delta is rebuilt between launches) and is not taken
+// in one that started in Delta mode.
+__device__ __forceinline__ void t2_block_end(const ChainDev &g, int &mode, int mode0,
+                                             bool &stop_early, int &blk_it, int &blk_acc,
+                                             int mb, int &cr, int &cs, int &wrow) {
+  if (blk_it < kHybBlock) return;
+  if (mode == 1 && (float)blk_acc < g.hyb_lo * (float)blk_it) {
+    if (mode0 == 1) {
+      mode = 0;
+      stop_early = true;
+    }
+  } else if (mode == 0 && g.hyb_lo > 0.0f && (float)blk_acc > 4.0f * g.hyb_lo * (float)blk_it) {
+    mode = 1;
+    decode_pair(g.N, mb, cr, cs);
+    wrow = -1;
+  }
+  blk_it = blk_acc = 0;
+}
+
 // One chain on the calling cluster.  Every CTA of the cluster must call it with
 // the same arguments.
 // tb: TMEM address of the calling thread's tile (lane group of its warp,
@@ -143,6 +167,8 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
   int8_t *a_s = reinterpret_cast<int8_t *>(smem + kT2OffRowAs);
   int8_t *o_r = reinterpret_cast<int8_t *>(smem + kT2OffRowBr);
   int8_t *o_s = reinterpret_cast<int8_t *>(smem + kT2OffRowBs);
+  int8_t *w_a = reinterpret_cast<int8_t *>(smem + kT2OffRowWa);
+  int8_t *w_b = reinterpret_cast<int8_t *>(smem + kT2OffRowWb);
   int4 *s_slot = reinterpret_cast<int4 *>(smem + kT2OffSlot);
   unsigned *s_ctl = reinterpret_cast<unsigned *>(smem + kT2OffCtl);
   float2 *s_tt = reinterpret_cast<float2 *>(smem + kT2OffTt);
@@ -186,9 +212,18 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     u0 = t >> 16;
     v0 = t & 0xFFFF;
   }
+  // Modes, as in the one-SM tier: 1 = proposals evaluated directly (Delta not
+  // maintained), 0 = read from Delta.  A launch that starts in direct mode
+  // returns when the acceptance rate calls for Delta (the host then rebuilds
+  // Delta in global memory and launches again); one that starts in Delta mode
+  // may switch to direct mode but not back.
+  int mode = (g.hyb_lo > 0.0f) ? g.st->mode : 0;
+  const int mode0 = mode;
+  bool tiles_valid = (mode0 == 0);  // the TMEM tiles hold Delta of the current p
+  bool delta_stale = false;         // a swap was accepted without updating Delta
   int tm_lo = 0x7FFFFFFF, tm_hi = -1;
 #pragma unroll 1
-  for (int q = 0; q < R / 4; ++q) {  // cells to TMEM, 4 rows at a time
+  for (int q = 0; q < R / 4 && mode0 == 0; ++q) {  // cells to TMEM, 4 rows at a time
     int Dq[16];
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii)
@@ -215,6 +250,15 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
   int pend_r = -1, pend_s = -1;
   unsigned long long tab_it = 0;
   int tab_len = 0;
+  int blk_it = 0, blk_acc = 0;  // iterations and accepts of the current block
+  bool stop_early = false;
+  int cr = 0, cs = 1;  // direct mode: pair of iteration it
+  int wrow = -1;       // direct mode: the row staged in w_a, w_b
+  if (mode == 1) decode_pair(N, mb, cr, cs);
+  if (tid == 0) {
+    c64[kC64DirIt] = 0;
+    c64[kC64DirAcc] = 0;
+  }
   cluster.sync();  // every CTA initialised before any remote write
 
   for (;;) {
@@ -239,10 +283,10 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
           row[k] = (k == r) ? o_r[s] : (k == s ? o_r[r] : o_r[k]);
       }
       // ---- recomputed rows/columns r,s -> the TMEM cells (warp-collective),
-      //      8 rows at a time ----
+      //      8 rows at a time (Delta mode) ----
       const bool col_hit = has_tile && ((r >= v0 && r < v0 + 4) || (s >= v0 && s < v0 + 4));
 #pragma unroll 1
-      for (int h = 0; h < R / 8; ++h) {
+      for (int h = 0; h < R / 8 && mode == 0; ++h) {
         const int uh = u0 + 8 * h;
         const bool row_hit = has_tile && ((r >= uh && r < uh + 8) || (s >= uh && s < uh + 8));
         if (!__any_sync(0xFFFFFFFFu, row_hit || col_hit)) continue;
@@ -274,10 +318,11 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       }
     }
     pend_r = -1;
-    if (it >= it_end || err) break;
+    if (it >= it_end || err || stop_early) break;
 
     // ================= scan one window =================
-    const int wlen = (int)min((unsigned long long)K, it_end - it);
+    // direct mode: the window stays in row cr (pairs (cr, cs .. N-1))
+    const int wlen = (int)min((unsigned long long)(mode == 1 ? min(K, N - cs) : K), it_end - it);
     const int jt0 = (it >= tab_it && it - tab_it < (unsigned long long)tab_len)
                         ? (int)(it - tab_it) : kTabMax;
     float Tw = 0.0f;
@@ -290,7 +335,76 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     }
     unsigned best = kNone;
     int bu = 0, bv = 0, bd = 0;
-    const bool scan_me = has_tile && meets_window(tm_lo, tm_hi, mb, wlen, M);
+    if (mode == 1) {
+      // ---- direct mode: each CTA evaluates the proposals (cr, s) whose row s
+      //      lies in its slice, eight lanes a proposal:
+      //      delta = 2 (<A_r, B'_s> + <A_s, B'_r> - d_r - d_s + 2 A_rs B'_rs) ----
+      if (wrow != cr) {  // a new row (the same decision in every CTA): from the
+                         // CTA that owns it, once every CTA's loop-top swap is done
+        cluster.sync();
+        const int q = cr / NV;
+        const int *ra = cluster.map_shared_rank(
+            reinterpret_cast<const int *>(s_A + (cr - q * NV) * S), q);
+        const int *rb = cluster.map_shared_rank(
+            reinterpret_cast<const int *>(s_B + (cr - q * NV) * S), q);
+        for (int w = tid; w < (S >> 2); w += nthreads) {
+          reinterpret_cast<int *>(w_a)[w] = ra[w];
+          reinterpret_cast<int *>(w_b)[w] = rb[w];
+        }
+        wrow = cr;
+      }
+      __syncthreads();  // window row staged; this CTA's B' swap of the loop top done
+      const int jlo = max(0, sv_lo - cs), jhi = min(wlen, sv_hi - cs);
+      const int per_pass = nthreads >> 3;  // eight lanes a proposal
+      for (int jb = jlo; jb < jhi; jb += per_pass) {  // the same passes in every warp
+        const int j = jb + (tid >> 3), sub = tid & 7;
+        const bool live = j < jhi;
+        int g1 = 0, g2 = 0;
+        if (live) {
+          const int s = cs + j;
+          const int4 *As4 = reinterpret_cast<const int4 *>(s_A + (s - sv_lo) * S);
+          const int4 *Bs4 = reinterpret_cast<const int4 *>(s_B + (s - sv_lo) * S);
+          const int4 *Ar4 = reinterpret_cast<const int4 *>(w_a);
+          const int4 *Br4 = reinterpret_cast<const int4 *>(w_b);
+          for (int c = sub; c < NC; c += 8) {
+            g1 = dot16(Ar4[c], Bs4[c], g1);
+            g2 = dot16(As4[c], Br4[c], g2);
+          }
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          g1 += __shfl_xor_sync(0xFFFFFFFFu, g1, o);
+          g2 += __shfl_xor_sync(0xFFFFFFFFu, g2, o);
+        }
+        if (live && sub == 0) {
+          const int s = cs + j;
+          const int dv = 2 * (g1 + g2 - s_d[cr] - s_d[s] + 2 * (int)w_a[s] * (int)w_b[s]);
+          unsigned acc = 0, unc = 0;
+          const int jt = jt0 + j;
+          if (dv <= 0) {
+            acc = 1;
+          } else if (jt < tab_len) {
+            const float2 b = s_tt[jt];
+            const float df = (float)dv;
+            if (df < b.x) acc = 1;
+            else if (!(df > b.y)) unc = 1;
+          } else if (dv <= thr) {
+            const unsigned o = pretest_cells(g.seed, g.stream, g.log2a_f, g.mrel, it, Tw, j,
+                                             0, 0, 0, dv, 0, 0, 0, 1u);
+            acc = o & 1u;
+            unc = (o >> 4) & 1u;
+          }
+          const unsigned key = ((unsigned)j << 1) | unc;
+          if ((acc | unc) && key < best) {
+            best = key;
+            bu = cr;
+            bv = s;
+            bd = dv;
+          }
+        }
+      }
+    }
+    const bool scan_me = mode == 0 && has_tile && meets_window(tm_lo, tm_hi, mb, wlen, M);
     if (__any_sync(0xFFFFFFFFu, scan_me)) {
 #pragma unroll 1
       for (int q = 0; q < R / 4; ++q) {
@@ -387,6 +501,12 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       if (mb >= M) mb -= M;
       it += (unsigned)wlen;
       K = min(K * 2, M);
+      if (mode == 1) {
+        if (tid == 0 && rank == 0) c64[kC64DirIt] += (unsigned)wlen;
+        decode_pair(N, mb, cr, cs);
+      }
+      blk_it += wlen;
+      t2_block_end(g, mode, mode0, stop_early, blk_it, blk_acc, mb, cr, cs, wrow);
       continue;
     }
     const int j = (int)(code >> 10);  // code = j | rank (4 bits) | warp (5) | undecided (1)
@@ -404,6 +524,12 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
         it += (unsigned)j + 1;
         mb += j + 1;
         if (mb >= M) mb -= M;
+        if (mode == 1) {
+          if (tid == 0 && rank == 0) c64[kC64DirIt] += (unsigned)j + 1;
+          decode_pair(N, mb, cr, cs);
+        }
+        blk_it += j + 1;
+        t2_block_end(g, mode, mode0, stop_early, blk_it, blk_acc, mb, cr, cs, wrow);
         continue;
       }
     }
@@ -419,6 +545,19 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     if (tid == 0 && rank == 0) {
       ++c64[kC64Accepts];
       c64[kC64Cost] += (unsigned long long)(long long)dlt;
+      if (mode == 1) {
+        c64[kC64DirIt] += (unsigned)j + 1;
+        ++c64[kC64DirAcc];
+      }
+    }
+    blk_it += j + 1;
+    ++blk_acc;
+    // direct mode: the row of the next window, old contents, fetched below
+    int ncr = r, ncs = s;
+    next_pair(N, ncr, ncs);
+    if (mode == 1) {
+      tiles_valid = false;
+      delta_stale = true;
     }
 
     // ---- stage (every CTA): rows r,s of A and of B' before the swap from
@@ -437,6 +576,17 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       int *lBr = reinterpret_cast<int *>(o_r), *lBs = reinterpret_cast<int *>(o_s);
       const int SW = S >> 2;
       int dr_part = 0, ds_part = 0;
+      if (mode == 1) {  // row ncr of A and B' before the swap
+        const int qn = ncr / NV;
+        const int *Na = cluster.map_shared_rank(
+            reinterpret_cast<const int *>(s_A + (ncr - qn * NV) * S), qn);
+        const int *Nb = cluster.map_shared_rank(
+            reinterpret_cast<const int *>(s_B + (ncr - qn * NV) * S), qn);
+        for (int w = tid; w < SW; w += nthreads) {
+          reinterpret_cast<int *>(w_a)[w] = Na[w];
+          reinterpret_cast<int *>(w_b)[w] = Nb[w];
+        }
+      }
       for (int w = tid; w < SW; w += nthreads) {
         const int ar = Ar[w], as = As[w], br = Br[w], bs = Bs[w];
         lAr[w] = ar;
@@ -478,6 +628,21 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     }
     __syncthreads();  // rows r,s, a, b, d, d_r, d_s complete
 
+    if (mode == 1) {
+      // ---- the next window's row under the new p: B'new_x = B'_pi(x) with
+      //      columns r,s exchanged (pi swaps r and s); A is constant ----
+      if (ncr == r || ncr == s) {
+        const int8_t *src = (ncr == r) ? o_s : o_r;
+        for (int k = tid; k < S; k += nthreads)
+          w_b[k] = (k == r) ? src[s] : (k == s ? src[r] : src[k]);
+      } else if (tid == 0) {
+        const int8_t t = w_b[r];
+        w_b[r] = w_b[s];
+        w_b[s] = t;
+      }
+      wrow = ncr;
+    }
+
     // ---- rows r,s of this slice under the new p, from dot products on B'
     //      before the swap plus the O(1) terms the swap changes:
     //      <A_r, B'new_v> = <A_r, B_v> + A_rs (B_vr - B_vs),
@@ -494,7 +659,7 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       const int4 *Br4 = reinterpret_cast<const int4 *>(o_r);
       const int4 *Bs4 = reinterpret_cast<const int4 *>(o_s);
       const int nw = nthreads >> 5;
-      for (int vq = sv_lo + 4 * warp; vq < sv_hi; vq += 4 * nw) {
+      for (int vq = sv_lo + 4 * warp; vq < sv_hi && mode == 0; vq += 4 * nw) {
         const int nk = min(4, sv_hi - vq);
         int gk[16];  // [k][<A_r,B_v>, <A_s,B_v>, <A_v,B_s>, <A_v,B_r>], v = vq + k
 #pragma unroll
@@ -568,7 +733,7 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       }
     }
     // ---- O(1) update of the TMEM cells (warp-collective), 8 rows at a time ----
-    if (__any_sync(0xFFFFFFFFu, has_tile)) {
+    if (mode == 0 && __any_sync(0xFFFFFFFFu, has_tile)) {
       const int4 av = *reinterpret_cast<const int4 *>(s_a + v0);
       const int4 bv = *reinterpret_cast<const int4 *>(s_b + v0);
 #pragma unroll 1
@@ -597,11 +762,16 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     }
     pend_r = r;
     pend_s = s;
+    if (mode == 1) {
+      cr = ncr;
+      cs = ncs;
+    }
+    t2_block_end(g, mode, mode0, stop_early, blk_it, blk_acc, mb, cr, cs, wrow);
   }
 
-  // ---- state back to global memory ----
+  // ---- state back to global memory (Delta only if the tiles are current) ----
 #pragma unroll 1
-  for (int q = 0; q < R / 4; ++q) {
+  for (int q = 0; q < R / 4 && tiles_valid; ++q) {
     int Dq[16];
     tmem_ld16(tb + 16 * q, Dq);
 #pragma unroll
@@ -631,11 +801,40 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       g.st->near_ties += c64[kC64Near];
       g.st->exact_evals += c64[kC64Exact];
       g.st->windows += c64[kC64Windows];
+      g.st->direct_iters += c64[kC64DirIt];
+      g.st->direct_accepts += c64[kC64DirAcc];
+      g.st->mode = mode;
+      if (tiles_valid) g.st->need_rebuild = 0;
+      else if (delta_stale) g.st->need_rebuild = 1;
       if (err) g.st->error = err;
     }
   }
   cluster.sync();  // no CTA leaves while others may still address its memory
 }
+
+// Delta of every pair from its definition under the chain's current B' and d in
+// global memory, Delta_uv = 2 (<A_u, B'_v> + <A_v, B'_u> - d_u - d_v + 2 A_uv B'_uv),
+// if the last cluster-tier launch left it stale (grid: ceil(N / blockDim) x N).
+__global__ void rebuild_delta_kernel(ChainDev g) {
+  if (!g.st->need_rebuild) return;
+  const int N = g.N, S = g.S;
+  const int u = blockIdx.y, v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v <= u || v >= N) return;
+  const int4 *Au = reinterpret_cast<const int4 *>(g.A + (size_t)u * S);
+  const int4 *Bu = reinterpret_cast<const int4 *>(g.Bp + (size_t)u * S);
+  const int4 *Av = reinterpret_cast<const int4 *>(g.A + (size_t)v * S);
+  const int4 *Bv = reinterpret_cast<const int4 *>(g.Bp + (size_t)v * S);
+  int guv = 0, gvu = 0;
+  for (int c = 0; c < (S >> 4); ++c) {
+    guv = dot16(__ldg(Au + c), Bv[c], guv);
+    gvu = dot16(__ldg(Av + c), Bu[c], gvu);
+  }
+  g.delta[pidx(N, u, v)] = 2 * (guv + gvu - g.d[u] - g.d[v] +
+                                2 * (int)g.A[(size_t)u * S + v] * (int)g.Bp[(size_t)u * S + v]);
+}
+
+// Delta in global memory is current again (after rebuild_delta_kernel).
+__global__ void clear_rebuild_kernel(ChainStatus *st) { st->need_rebuild = 0; }
 
 __global__ void __launch_bounds__(kT2Threads, 1)
     sa_tier2_kernel(ChainDev g, unsigned long long it_end) {

@@ -285,6 +285,45 @@ def test_n1024_grid_workload_prefix_matches_oracle():
     assert_same(gs, os_, gd, od)
 
 
+@pytest.mark.parametrize("N,rate", [(300, "0"), (300, "1e-9"), (300, "2e-3"), (300, "1.0"),
+                                    (600, "1.0"), (600, "2e-3"), (280, "1e-9")])
+def test_cluster_direct_and_delta_modes_give_the_same_trajectory(N, rate, monkeypatch):
+    """The cluster tier's direct mode (each CTA evaluates the window's proposals
+    whose row lies in its slice; Delta not maintained, rebuilt between launches)
+    against the oracle.  rate = 0: Delta throughout; 1e-9: direct throughout;
+    2e-3: the default; 1.0: direct for the first block, then Delta (the launch
+    stops, Delta is rebuilt, a second launch continues).  Runs split across
+    launches; Delta compared at the end."""
+    monkeypatch.setenv("QAPSA_CLUSTER_HYBRID_RATE", rate)
+    A, B, p0 = instances.taixxa_like(N, 47)
+    I = 10 ** 7
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=I, seed=47, stream=3,
+                                     oracle_iters=60000, splits=[1, 29999, 30000])
+    info = g.info()
+    assert info["tier"] == 2
+    assert os_["accepts"] > 1000
+    assert_same(gs, os_, gd, od)
+    if rate == "0":
+        assert info["direct_iters"] == 0
+    elif rate == "1.0":
+        assert 0 < info["direct_iters"] < 60000
+    else:
+        assert info["direct_iters"] > 30000
+
+
+def test_cluster_direct_mode_cold_run_matches_oracle(monkeypatch):
+    """A whole short schedule on the cluster tier with the default switch point:
+    direct mode through the hot part, Delta mode (after a rebuild) through the
+    cold part, the final state and Delta against the oracle."""
+    A, B, p0 = instances.taixxa_like(290, 48)
+    I = 200000
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=I, seed=48,
+                                     splits=[70000, 70000, I - 140000])
+    info = g.info()
+    assert info["tier"] == 2 and 0 < info["direct_iters"] < I
+    assert_same(gs, os_, gd, od)
+
+
 @pytest.mark.parametrize("rate", ["0", "1e-9", "5e-4", "1.0"])
 def test_direct_and_delta_modes_give_the_same_trajectory(rate, monkeypatch):
     """Proposals evaluated directly or read from the maintained Delta: the same
