@@ -576,7 +576,7 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
     if (stop > end) stop = end;
     if (h->tier == 2) {
       // With the direct mode enabled a launch may leave Delta in global memory
-      // stale (it ended in direct mode) or stop early to switch to Delta mode:
+      // stale (it ended in direct mode) or stop early to resume Delta mode:
       // rebuild Delta if flagged, and launch again to the same end (a no-op if
       // the first launch got there).  The second launch starts in Delta mode or
       // at the end, so it never stops early.
@@ -769,13 +769,6 @@ int qap_batch_create(const qap_problem *probs, int32_t count, qap_batch **out) {
       return rc;
     }
     b->h.push_back(h);
-    if (h->tier == 2) {  // the persistent cluster launch keeps Delta throughout
-      h->dev.hyb_lo = 0.0f;
-      if ((e = cudaMemsetAsync(&h->st->mode, 0, sizeof(int), b->stream)) != cudaSuccess) {
-        free_batch(b);
-        return cuda_fail(e, "cudaMemsetAsync");
-      }
-    }
     BatchChain bc{};
     bc.g = h->dev;
     bc.it_end = 0;

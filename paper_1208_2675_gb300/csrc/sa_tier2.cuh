@@ -14,7 +14,13 @@
 //          table: shared memory of every CTA (each CTA keeps its own copy and
 //          updates it identically).
 //
-// One accepted swap costs two cluster barriers and one CTA barrier:
+// While many proposals are accepted (block acceptance above g.hyb_lo) the
+// chain runs in direct mode instead: Delta is not maintained, each CTA
+// evaluates the window's proposals whose second row lies in its slice, and an
+// accepted swap only updates d, p and B'; the tiles are rebuilt from their
+// definition when Delta mode resumes and before the state is stored.
+//
+// In Delta mode one accepted swap costs two cluster barriers and one CTA barrier:
 //   scan    each CTA tests its tiles in the window; warp winners post
 //           atomicMin(code) into every CTA's key word (DSMEM)  -> cluster barrier
 //   stage   (every CTA) rows r,s of A and of B' before the swap are read from
@@ -119,17 +125,18 @@ __device__ __forceinline__ int dot16(int4 x, int4 y, int acc) {
 
 // Mode decisions of the cluster tier at the end of a block of kHybBlock
 // iterations (every thread of every CTA alike): to direct mode above
-// 4 g.hyb_lo; back to Delta mode below g.hyb_lo, which ends a launch that
-// started in direct mode (Delta is rebuilt between launches) and is not taken
-// in one that started in Delta mode.
-__device__ __forceinline__ void t2_block_end(const ChainDev &g, int &mode, int mode0,
-                                             bool &stop_early, int &blk_it, int &blk_acc,
+// 4 g.hyb_lo, back to Delta mode (Delta rebuilt first) below g.hyb_lo where
+// allow_back.  With the host's rebuild a launch stops to resume Delta mode, and
+// only one that started in direct mode may stop: the host queues two launches
+// per piece of a run, and the second starts in Delta mode or at the end.
+__device__ __forceinline__ void t2_block_end(const ChainDev &g, int &mode, bool &rebuild,
+                                             bool allow_back, int &blk_it, int &blk_acc,
                                              int mb, int &cr, int &cs, int &wrow) {
   if (blk_it < kHybBlock) return;
   if (mode == 1 && (float)blk_acc < g.hyb_lo * (float)blk_it) {
-    if (mode0 == 1) {
+    if (allow_back) {
       mode = 0;
-      stop_early = true;
+      rebuild = true;  // in the tiles, or (host rebuild) by stopping the launch
     }
   } else if (mode == 0 && g.hyb_lo > 0.0f && (float)blk_acc > 4.0f * g.hyb_lo * (float)blk_it) {
     mode = 1;
@@ -139,10 +146,52 @@ __device__ __forceinline__ void t2_block_end(const ChainDev &g, int &mode, int m
   blk_it = blk_acc = 0;
 }
 
+// Delta of the calling thread's tile from its definition into its TMEM cells,
+// Delta_uv = 2 (<A_u, B'_v> + <A_v, B'_u> - d_u - d_v + 2 A_uv B'_uv), from the
+// rows of A and B' in global memory (every CTA has written its B' rows there)
+// and d.  Every thread of the cluster calls it (the TMEM stores are
+// warp-collective), from one call site: when Delta mode resumes and before the
+// state is stored after direct mode.
+__device__ __forceinline__ void t2_rebuild_tile(const int8_t *A, const int8_t *Bp, const int *d,
+                                             int N, int S, int u0, int v0, bool has_tile,
+                                             unsigned tb) {
+  const int NC = S >> 4;
+#pragma unroll 1
+  for (int q = 0; q < kT2R / 4; ++q) {
+    int Dq[16];
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int u = u0 + 4 * q + ii, v = v0 + c;
+        int val = 0;
+        if (has_tile && u < v && v < N) {
+          const int4 *Au = reinterpret_cast<const int4 *>(A + (size_t)u * S);
+          const int4 *Bu = reinterpret_cast<const int4 *>(Bp + (size_t)u * S);
+          const int4 *Av = reinterpret_cast<const int4 *>(A + (size_t)v * S);
+          const int4 *Bv = reinterpret_cast<const int4 *>(Bp + (size_t)v * S);
+          int guv = 0, gvu = 0;
+          for (int k = 0; k < NC; ++k) {
+            guv = dot16(__ldg(Au + k), __ldcg(Bv + k), guv);
+            gvu = dot16(__ldg(Av + k), __ldcg(Bu + k), gvu);
+          }
+          val = 2 * (guv + gvu - d[u] - d[v] +
+                     2 * (int)A[(size_t)u * S + v] * (int)__ldcg(Bp + (size_t)u * S + v));
+        }
+        Dq[4 * ii + c] = val;
+      }
+    tmem_st16(tb + 16 * q, Dq);
+  }
+}
+
 // One chain on the calling cluster.  Every CTA of the cluster must call it with
 // the same arguments.
 // tb: TMEM address of the calling thread's tile (lane group of its warp,
-// first of the warp's 4R columns).
+// first of the warp's 4R columns).  HostRebuild: when Delta mode must resume
+// after direct mode the launch stops and the host's queued rebuild_delta_kernel
+// and second launch continue (the single-chain kernel); otherwise the tiles
+// are rebuilt inside the kernel (the persistent batch kernel).
+template <bool HostRebuild>
 __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
                                              unsigned long long it_end,
                                              unsigned char *smem, unsigned tb) {
@@ -213,17 +262,14 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     v0 = t & 0xFFFF;
   }
   // Modes, as in the one-SM tier: 1 = proposals evaluated directly (Delta not
-  // maintained), 0 = read from Delta.  A launch that starts in direct mode
-  // returns when the acceptance rate calls for Delta (the host then rebuilds
-  // Delta in global memory and launches again); one that starts in Delta mode
-  // may switch to direct mode but not back.
+  // maintained), 0 = read from Delta; the tiles are rebuilt from their
+  // definition when Delta mode resumes and before the state is stored.
   int mode = (g.hyb_lo > 0.0f) ? g.st->mode : 0;
-  const int mode0 = mode;
-  bool tiles_valid = (mode0 == 0);  // the TMEM tiles hold Delta of the current p
-  bool delta_stale = false;         // a swap was accepted without updating Delta
+  const bool allow_back = !HostRebuild || mode == 1;
+  bool tiles_valid = (mode == 0);  // the TMEM tiles hold Delta of the current p
   int tm_lo = 0x7FFFFFFF, tm_hi = -1;
 #pragma unroll 1
-  for (int q = 0; q < R / 4 && mode0 == 0; ++q) {  // cells to TMEM, 4 rows at a time
+  for (int q = 0; q < R / 4; ++q) {  // cells to TMEM, 4 rows at a time
     int Dq[16];
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii)
@@ -233,12 +279,12 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
         Dq[4 * ii + c] = 0;
         if (has_tile && u < v && v < N) {
           const int m = pidx(N, u, v);
-          Dq[4 * ii + c] = g.delta[m];
+          if (tiles_valid) Dq[4 * ii + c] = g.delta[m];
           tm_lo = min(tm_lo, m);
           tm_hi = max(tm_hi, m);
         }
       }
-    tmem_st16(tb + 16 * q, Dq);
+    if (tiles_valid) tmem_st16(tb + 16 * q, Dq);
   }
   const int NC = S >> 4;  // 16-byte chunks of a row
 
@@ -251,7 +297,7 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
   unsigned long long tab_it = 0;
   int tab_len = 0;
   int blk_it = 0, blk_acc = 0;  // iterations and accepts of the current block
-  bool stop_early = false;
+  bool rebuild = false;         // Delta mode resumes: tiles from their definition first
   int cr = 0, cs = 1;  // direct mode: pair of iteration it
   int wrow = -1;       // direct mode: the row staged in w_a, w_b
   if (mode == 1) decode_pair(N, mb, cr, cs);
@@ -259,8 +305,24 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     c64[kC64DirIt] = 0;
     c64[kC64DirAcc] = 0;
   }
+  // every CTA's B' rows to global memory, then every thread's tile from its
+  // definition (all threads of the cluster together)
+  auto rebuild_tiles = [&]() {
+    __syncthreads();  // this CTA's B' swap of the loop top is complete
+    const int n4 = max(0, sv_hi - sv_lo) * (S >> 4);
+    int4 *gB4 = reinterpret_cast<int4 *>(g.Bp + (size_t)sv_lo * S);
+    const int4 *lB4 = reinterpret_cast<const int4 *>(s_B);
+    for (int i = tid; i < n4; i += nthreads) gB4[i] = lB4[i];
+    __threadfence();
+    cluster.sync();  // every CTA's rows written
+    t2_rebuild_tile(g.A, g.Bp, s_d, N, S, u0, v0, has_tile, tb);
+    cluster.sync();  // every CTA has read them
+    tiles_valid = true;
+  };
   cluster.sync();  // every CTA initialised before any remote write
 
+  bool last = false;
+  for (;;) {  // segments: a rebuild of the tiles between them, out of the window loop
   for (;;) {
     if (pend_r >= 0) {
       const int r = pend_r, s = pend_s;
@@ -286,7 +348,7 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       //      8 rows at a time (Delta mode) ----
       const bool col_hit = has_tile && ((r >= v0 && r < v0 + 4) || (s >= v0 && s < v0 + 4));
 #pragma unroll 1
-      for (int h = 0; h < R / 8 && mode == 0; ++h) {
+      for (int h = 0; h < R / 8 && mode == 0 && !rebuild; ++h) {
         const int uh = u0 + 8 * h;
         const bool row_hit = has_tile && ((r >= uh && r < uh + 8) || (s >= uh && s < uh + 8));
         if (!__any_sync(0xFFFFFFFFu, row_hit || col_hit)) continue;
@@ -318,7 +380,8 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       }
     }
     pend_r = -1;
-    if (it >= it_end || err || stop_early) break;
+    last = it >= it_end || err;
+    if (last || rebuild) break;
 
     // ================= scan one window =================
     // direct mode: the window stays in row cr (pairs (cr, cs .. N-1))
@@ -506,7 +569,7 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
         decode_pair(N, mb, cr, cs);
       }
       blk_it += wlen;
-      t2_block_end(g, mode, mode0, stop_early, blk_it, blk_acc, mb, cr, cs, wrow);
+      t2_block_end(g, mode, rebuild, allow_back, blk_it, blk_acc, mb, cr, cs, wrow);
       continue;
     }
     const int j = (int)(code >> 10);  // code = j | rank (4 bits) | warp (5) | undecided (1)
@@ -529,7 +592,7 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
           decode_pair(N, mb, cr, cs);
         }
         blk_it += j + 1;
-        t2_block_end(g, mode, mode0, stop_early, blk_it, blk_acc, mb, cr, cs, wrow);
+        t2_block_end(g, mode, rebuild, allow_back, blk_it, blk_acc, mb, cr, cs, wrow);
         continue;
       }
     }
@@ -555,10 +618,7 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     // direct mode: the row of the next window, old contents, fetched below
     int ncr = r, ncs = s;
     next_pair(N, ncr, ncs);
-    if (mode == 1) {
-      tiles_valid = false;
-      delta_stale = true;
-    }
+    if (mode == 1) tiles_valid = false;
 
     // ---- stage (every CTA): rows r,s of A and of B' before the swap from
     //      the CTAs that own them; a, b, d, d_r, d_s from them ----
@@ -766,10 +826,22 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       cr = ncr;
       cs = ncs;
     }
-    t2_block_end(g, mode, mode0, stop_early, blk_it, blk_acc, mb, cr, cs, wrow);
+    t2_block_end(g, mode, rebuild, allow_back, blk_it, blk_acc, mb, cr, cs, wrow);
+  }
+    // tiles from their definition (the loop top's B' swap done): Delta mode
+    // resumes, or the state is about to be stored and Delta was not maintained
+    if constexpr (HostRebuild) {
+      break;  // Delta in global memory is rebuilt by the host's queued kernel
+    } else {
+      if (rebuild || !tiles_valid) {
+        rebuild_tiles();
+        rebuild = false;
+      }
+      if (last) break;
+    }
   }
 
-  // ---- state back to global memory (Delta only if the tiles are current) ----
+  // ---- state back to global memory (Delta if the tiles hold it) ----
 #pragma unroll 1
   for (int q = 0; q < R / 4 && tiles_valid; ++q) {
     int Dq[16];
@@ -804,8 +876,7 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
       g.st->direct_iters += c64[kC64DirIt];
       g.st->direct_accepts += c64[kC64DirAcc];
       g.st->mode = mode;
-      if (tiles_valid) g.st->need_rebuild = 0;
-      else if (delta_stale) g.st->need_rebuild = 1;
+      if (!tiles_valid) g.st->need_rebuild = 1;  // host rebuild only (else valid)
       if (err) g.st->error = err;
     }
   }
@@ -814,7 +885,8 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
 
 // Delta of every pair from its definition under the chain's current B' and d in
 // global memory, Delta_uv = 2 (<A_u, B'_v> + <A_v, B'_u> - d_u - d_v + 2 A_uv B'_uv),
-// if the last cluster-tier launch left it stale (grid: ceil(N / blockDim) x N).
+// if the last single-chain cluster launch left it stale (grid:
+// ceil(N / blockDim) x N).
 __global__ void rebuild_delta_kernel(ChainDev g) {
   if (!g.st->need_rebuild) return;
   const int N = g.N, S = g.S;
@@ -841,7 +913,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_tmem;
   const unsigned tb = tile_tmem_acquire(&s_tmem, 4 * kT2R);
-  t2_run_chain(g, it_end, smem, tb);
+  t2_run_chain<true>(g, it_end, smem, tb);
   tile_tmem_release(&s_tmem);
 }
 
@@ -862,7 +934,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
     cluster.sync();  // every CTA has read the index before it can change
     if (k >= n) break;
     const BatchChain &bc = chains[order[k]];
-    t2_run_chain(bc.g, bc.it_end, smem, tb);
+    t2_run_chain<false>(bc.g, bc.it_end, smem, tb);
   }
   tile_tmem_release(&s_tmem);
 }
