@@ -204,7 +204,10 @@ QAP_EXPORT void qap_batch_destroy(qap_batch *b);
  * paper has no counterpart; each request's result equals qap_sa_run's for the
  * same problem.                                                               */
 typedef struct qap_server_cfg {
-  int32_t max_sms;          /* SMs the server may fill (0 = all)               */
+  int32_t max_sms;          /* SMs the server may fill with chains (0 = all but
+                               four, which stay free for the set-up and
+                               rebuild kernels of admissions: an SM holding a
+                               chain has no room left for them)             */
   uint32_t reserved;        /* must be 0                                       */
   uint64_t mem_budget_bytes;/* device bytes for chains (0 = 80 % of free)      */
 } qap_server_cfg;

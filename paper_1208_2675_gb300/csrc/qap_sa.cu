@@ -1018,6 +1018,10 @@ extern "C" int qap_sa_setup_noalloc(const int32_t *A, const int32_t *B,
 // ------------------------------------------------------------------------- //
 cudaStream_t qapsa_handle_stream(qap_sa *h) { return h ? h->stream : nullptr; }
 
+void qapsa_keep_delta_mode(qap_sa *h) {
+  if (h && h->tier == 2) h->dev.hyb_lo = 0.0f;
+}
+
 int qapsa_sms_for(int N) { return N <= max_n_tier1() ? 1 : tier2_cluster(N); }
 
 size_t qapsa_bytes_for(int N) {

@@ -95,6 +95,7 @@ bool launch(qap_server *s, const std::shared_ptr<Request> &r) {
   qap_sa *h = nullptr;
   int st = qap_sa_create(r->A.data(), r->B.data(), r->N, r->p0.data(), &r->sched,
                          r->seed, &h);
+  if (st == QAP_OK) qapsa_keep_delta_mode(h);  // one launch per piece: SMs held
   if (st == QAP_OK) st = qap_sa_run_async(h, r->iters);
   cudaEvent_t ev = nullptr;
   if (st == QAP_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
@@ -191,7 +192,13 @@ int qap_server_start(const qap_server_cfg *cfg, qap_server **out) {
     delete s;
     return QAP_E_CUDA;
   }
-  s->max_sms = (s->cfg.max_sms > 0 && s->cfg.max_sms < sms) ? s->cfg.max_sms : sms;
+  // Chains fill at most all SMs but a few: an SM that holds one (255 registers
+  // a thread at 256 threads, or 96 at 640) has no room left for another block,
+  // so the set-up kernels of an admission -- which the worker waits for -- and
+  // the cluster tier's Delta rebuilds need SMs that no chain occupies.
+  constexpr int kFreeSMs = 4;
+  s->max_sms = (s->cfg.max_sms > 0 && s->cfg.max_sms < sms) ? s->cfg.max_sms
+                                                             : (sms > 2 * kFreeSMs ? sms - kFreeSMs : sms);
   s->budget = s->cfg.mem_budget_bytes ? (size_t)s->cfg.mem_budget_bytes
                                       : (size_t)(0.8 * (double)free_b);
   // Grow the device's default pool once, now, while nothing runs: growing it
