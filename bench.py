@@ -34,7 +34,7 @@ WORKLOADS = {
                  # sa_tier1_kernel<256> on this instance (2e6 iterations): the chain
                  # state and the code are read once per launch and everything stays
                  # on chip, so a launch of any length moves the same bytes
-                 dram_bytes_per_launch=993792,
+                 dram_bytes_per_launch=489984,
                  traffic_basis="ncu capture of one 2e6-iteration launch of the same "
                                "kernel on this instance; independent of the launch's "
                                "length (state on chip)"),
