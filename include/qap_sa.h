@@ -105,7 +105,11 @@ QAP_EXPORT int qap_sa_create_device(const int32_t *A, const int32_t *B, int32_t 
  * (double)delta < -(T(it) * log(u)) in IEEE binary64); on acceptance p, the
  * cost and Delta are updated.  Windows of consecutive proposals are tested in
  * parallel and the first accepted one in sequential order is taken
- * (section 3 (ii)), so the trajectory equals the sequential one.
+ * (section 3 (ii)), so the trajectory equals the sequential one.  While the
+ * acceptance rate is high the swap cost of a proposal is evaluated directly
+ * from A and B' instead of being read from Delta (the same exact integer) and
+ * Delta is rebuilt from its definition before it is read again, so Delta is
+ * always current between calls (qap_sa_delta).
  * run(a); run(b) gives the same state as run(a + b).  Blocks until done.
  * Returns QAP_E_RANGE if it + iters > total_iters.                          */
 QAP_EXPORT int qap_sa_run(qap_sa *h, uint64_t iters);

@@ -11,17 +11,20 @@
 //          128-bit loads in the rows-r,s recompute);
 //   a, b, d, p, the two recomputed rows, per-warp winner slots: shared memory.
 //
-// One accepted swap costs three block barriers:
+// With Delta maintained (low acceptance) one accepted swap costs three block
+// barriers:
 //   scan    every thread tests its tile's cells that fall in the window
 //           [it, it + K) of the cyclic proposal order against Eq. (2);
 //           redux.min per warp, atomicMin across warps      -> barrier
 //   stage   a_k = A_rk - A_sk, b_k = B'_sk - B'_rk (B' before the swap),
 //           d_k, the row/column swap of B' (Eq. 3), p        -> barrier
-//   update  O(1) update of every register cell; rows r,s from their
-//           definition through dp4a dot products into shared memory
-//                                                           -> barrier
-// and the recomputed rows are copied into the owning registers at the top of
-// the next scan (each thread reads only its own registers there).
+//   update  O(1) update of every tile cell; rows r,s from their definition
+//           through dp4a dot products into shared memory     -> barrier
+// and the recomputed rows are copied into the owning tiles at the top of the
+// next scan (each thread touches only its own tile there).  At higher
+// acceptance the proposals are evaluated directly (t1_run_chain), by the whole
+// CTA (two barriers per accepted swap) or, while many are accepted, by one
+// warp alone (t1_warp_run, no block barrier).
 #pragma once
 #include "sa_common.cuh"
 #include "sa_tmem.cuh"
