@@ -43,7 +43,9 @@ struct ChainDev {
   int N;        // problem size
   int S;        // row stride of A and B' in bytes (16 x odd, zero padded)
   int M;        // N(N-1)/2 pairs
-  int tpv;      // threads per row in the rows-r,s recompute (power of two)
+  int tpv;      // the host's threads per row for the rows-r,s recompute; the
+                // kernels derive their own (the field keeps the parameter
+                // layout the kernels were tuned with)
   int ntiles;   // Delta tiles (one per thread of the SA kernel)
   const int *tiles;  // ntiles entries: first row << 16 | first column
   const int8_t *A;   // N*S, constant
