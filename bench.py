@@ -19,6 +19,7 @@ import multiprocessing as mp
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -110,10 +111,12 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the samples go to QAPSA_CLOCKS_CSV if set, else to a temporary file
+        self.path = os.environ.get("QAPSA_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), f"qapsa_clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
