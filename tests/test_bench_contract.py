@@ -1,0 +1,50 @@
+"""The benchmark's JSON line, on the CPU: the reference arm (the oracle timed on
+the host cores) prints one line with the keys a caller of bench.py reads, and
+the workload table names what the bench measures."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def reference_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600, check=True, cwd=ROOT)
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    return json.loads(lines[0])
+
+
+def test_reference_arm_prints_the_contract_keys(reference_line):
+    d = reference_line
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference"
+    assert d["metric"] == "sa_iterations_per_sec" and d["unit"] == "iter/s"
+    assert d["higher_is_better"] is True and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert "workload" in d["config"]
+
+
+def test_workloads_name_the_measured_configurations(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    w = bench.WORKLOADS
+    assert w["n100"]["N"] == 100 and w["n100"]["I"] == 10 ** 8
+    assert w["n256"]["N"] == 256 and w["n256"]["I"] == 10 ** 9
+    assert w["batch512"]["count"] == 512
+    assert (w["batch512"]["n_lo"], w["batch512"]["n_hi"]) == (20, 300)
+    assert (w["serve"]["n_lo"], w["serve"]["n_hi"]) == (30, 600)
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    args = bench.parse()  # no flags: one GPU, the N = 100 chain, >= 3 warm-up steps
+    assert args.gpus == 1 and args.workload == "n100" and args.warmup >= 3
