@@ -1,12 +1,12 @@
 // sa_tier2.cuh -- tier 2 of the SA loop (Paul, arXiv:1208.2675, sections 2.2
 // and 3): one chain on a thread-block cluster of C CTAs (C <= 16), for N above
-// what one SM holds (up to ~1100).
+// what one SM holds (up to 1136).
 //
 // Where the data lives during a run:
 //   Delta  Tensor Memory of the cluster: the R x 4 tiles of the upper triangle
 //          are split into C contiguous ranges, one per CTA (<= 640 tiles each);
 //          thread t keeps its tile in its own TMEM lane, 4R columns, and moves
-//          it to registers 4 rows (16 cells) at a time;
+//          it to registers 4 or 8 rows (16 or 32 cells) at a time;
 //   A, B'  shared memory of the cluster: CTA c holds the int8 rows v of its
 //          slice [c*NV, (c+1)*NV) of both matrices (row stride S), loaded once
 //          per launch; B' rows are written back at the end;
@@ -31,7 +31,7 @@
 //           16-byte stores); O(1) update of the TMEM cells    -> cluster barrier
 // and at the top of the next scan each CTA swaps columns r,s of its B' rows (and
 // rewrites rows r,s if it owns them) and copies the recomputed rows into its
-// registers.  All control decisions are computed identically in every CTA from
+// TMEM tiles.  All control decisions are computed identically in every CTA from
 // the same data, so the CTAs never diverge and every barrier is reached by all.
 // The barriers are hardware cluster barriers: there is no software spin-wait.
 #pragma once
@@ -47,7 +47,7 @@ namespace cg = cooperative_groups;
 constexpr int kT2Threads = 640;
 constexpr int kT2R = 16;
 constexpr int kT2MaxCluster = 16;
-constexpr int kT2Tpv = 8;      // threads per slice row in the dot products
+constexpr int kT2Tpv = 8;      // the host's ChainDev::tpv (the kernels do not read it)
 constexpr int kT2MaxN = 1136;  // 16 CTAs x 640 tiles of 16 x 4 hold N <= 1136
 
 // Shared memory of one CTA.  Everything but the slices of A and B' sits at
@@ -707,7 +707,7 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     //      before the swap plus the O(1) terms the swap changes:
     //      <A_r, B'new_v> = <A_r, B_v> + A_rs (B_vr - B_vs),
     //      <A_v, B'new_r> = <A_v, B_s> + (A_vs - A_vr) B_rs, and symmetrically.
-    //      Warp w takes slice rows vq .. vq+3 (vq = sv_lo + 4w, + 4 warps ...),
+    //      Warp w takes slice rows vq .. vq+3 (vq = sv_lo + 4w, then 4 x warps on),
     //      its lanes the 16-byte chunks, so rows r,s of A and B' are read once
     //      per four slice rows; the four results are posted into every CTA as
     //      one 16-byte store per row of values ----
