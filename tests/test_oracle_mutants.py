@@ -1,10 +1,12 @@
 """Planted mistakes in the oracle are caught by its pins.
 
 Each mutant is a copy of oracle/qap_oracle.c with one plausible mistake (a
-dropped term, a wrong sign or index, a transposed operand, a wrong constant),
+dropped term, a wrong sign or index, a transposed operand, a wrong constant, a
+wrong schedule parameter),
 compiled on the CPU into a temporary library.  The checks below use only
 formulations independent of the oracle (Eq. (1) over locations, brute-force
-swap costs, Eq. (2) in exponential form, published Philox vectors); every
+swap costs, Eq. (2) in exponential form, published Philox vectors, the
+schedule's parameters from their definitions); every
 mutant must fail at least one of them, and the unmutated source must pass all.
 
 Not listed: accepting only delta < 0 outright instead of delta <= 0 -- an
@@ -44,6 +46,12 @@ MUTANTS = {
     "schedule_order": ("  for (int b = 7; b >= 0; --b) T = T * S->P[b][(it >> (8 * b)) & 0xFFu];",
                        "  for (int b = 7; b >= 0; --b) T = T * S->P[7 - b][(it >> (8 * b)) & 0xFFu];"),
     "cursor_order": ("  c->cur_s++;\n  if (c->cur_s == c->N) {", "  c->cur_s += 2;\n  if (c->cur_s >= c->N) {"),
+    "t0_mean_divisor": ("(double)sum / (double)c->M", "(double)sum / (double)c->N"),
+    "tf_not_relative": ("    Tf = tf * T0;\n  }", "    Tf = tf;\n  }"),
+    "alpha_exponent": ("pow(Tf / T0, 1.0 / (double)(I - 1))", "pow(Tf / T0, 1.0 / (double)(I))"),
+    "philox_multiplier": ("const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;",
+                          "const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D55u;"),
+    "philox_key_word": ("uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi1 ^ c1 ^ k1;"),
 }
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -136,6 +144,14 @@ def _pins_hold(L) -> bool:
     T0, Tf, al = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     L.orc_chain_schedule(h, ctypes.byref(T0), ctypes.byref(Tf), ctypes.byref(al))
     pairs = [(r, s) for r in range(N) for s in range(r + 1, N)]
+    # the schedule's parameters from their definitions: T0 = 0.5 mean |Delta_0|
+    # over the M pairs (brute-force swap costs), Tf = 1e-2 T0, alpha = (Tf/T0)^(1/(I-1))
+    c0 = _loc_cost(A, B, p0)
+    sum_abs = sum(abs(_loc_cost(A, B, _swapped(p0, r, s)) - c0) for r, s in pairs)
+    if T0.value != 0.5 * (sum_abs / len(pairs)) or Tf.value != 1e-2 * T0.value:
+        return False
+    if abs(al.value / (Tf.value / T0.value) ** (1.0 / (I - 1)) - 1.0) > 1e-12:
+        return False
     q = np.array(p0, copy=True)
     for it in range(I):
         r, s = pairs[it % len(pairs)]
