@@ -80,6 +80,12 @@ def lib() -> ctypes.CDLL:
         L.orc_chain_set_log.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
         L.orc_chain_get_log.restype = ctypes.c_uint64
         L.orc_chain_get_log.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_uint64]
+        L.orc_chain_set_near_log.restype = None
+        L.orc_chain_set_near_log.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+        L.orc_chain_get_near_log.restype = ctypes.c_uint64
+        L.orc_chain_get_near_log.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_uint64]
+        L.orc_chain_accepts.restype = ctypes.c_int32
+        L.orc_chain_accepts.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64]
         L.orc_chain_schedule.restype = None
         L.orc_chain_schedule.argtypes = [ctypes.c_void_p, _f64p, _f64p, _f64p]
         L.orc_chain_temperature.restype = ctypes.c_double
@@ -178,6 +184,7 @@ class Chain:
         if log_cap:
             lib().orc_chain_set_log(self._h, int(log_cap))
         self._log_cap = int(log_cap)
+        lib().orc_chain_set_near_log(self._h, 8)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -215,6 +222,16 @@ class Chain:
 
     def check_failures(self) -> int:
         return int(lib().orc_chain_check_failures(self._h))
+
+    def accepts(self, delta: int, it: int) -> bool:
+        """Eq. (2) (reading R3) for swap cost delta proposed at iteration it."""
+        return bool(lib().orc_chain_accepts(self._h, int(delta), int(it)))
+
+    def near_tie_log(self):
+        """(iteration indices of the first near-ties (up to 8), total count)."""
+        out = np.zeros(8, dtype=np.uint64)
+        n = lib().orc_chain_get_near_log(self._h, _ptr(out, _u64p), 8)
+        return out[:min(n, 8)], int(n)
 
     def accept_log(self) -> np.ndarray:
         cap = max(self._log_cap, 1)

@@ -32,6 +32,10 @@
  *                           or the traditional SA of section 2.1 (delta from
  *                           scratch for every proposal).
  *
+ * Each side counts the binary64 tests of Eq. (2) with |delta + T ln u| below
+ * 1e-9 T ("near-ties", where two libm logs could decide differently) and logs
+ * the iterations of the first ones (orc_chain_set_near_log).
+ *
  * Readings where the paper is silent (each is stated where it is used):
  *   R1 proposals: sequential cyclic enumeration of pairs r<s, row-major,
  *      pair(it) = pair number (it mod M), M = N(N-1)/2 (sec. 2.1, sec. 3(ii)).
@@ -227,6 +231,8 @@ typedef struct {
   int64_t check_failures;
   uint64_t *log;        /* iteration index of each accepted swap */
   uint64_t log_cap, log_n;
+  uint64_t *nlog;       /* iteration index of each near-tie (R3) */
+  uint64_t nlog_cap;
 } orc_chain;
 
 static void orc_pair_of(int32_t N, int64_t m, int32_t *r, int32_t *s) {
@@ -287,6 +293,7 @@ EXPORT void orc_chain_destroy(orc_chain *c) {
   free(c->p);
   free(c->D);
   free(c->log);
+  free(c->nlog);
   free(c);
 }
 
@@ -307,6 +314,22 @@ EXPORT uint64_t orc_chain_get_log(const orc_chain *c, uint64_t *out,
   uint64_t n = c->log_n < cap ? c->log_n : cap;
   if (n) memcpy(out, c->log, sizeof(uint64_t) * n);
   return c->log_n;
+}
+
+/* The iteration indices of the first near-ties (cap of them are kept; the
+ * count, near_ties, is kept in full). */
+EXPORT void orc_chain_set_near_log(orc_chain *c, uint64_t cap) {
+  free(c->nlog);
+  c->nlog = cap ? (uint64_t *)malloc(sizeof(uint64_t) * cap) : NULL;
+  c->nlog_cap = cap;
+}
+
+EXPORT uint64_t orc_chain_get_near_log(const orc_chain *c, uint64_t *out,
+                                       uint64_t cap) {
+  uint64_t n = c->near_ties < c->nlog_cap ? c->near_ties : c->nlog_cap;
+  if (n > cap) n = cap;
+  if (n) memcpy(out, c->nlog, sizeof(uint64_t) * n);
+  return c->near_ties;
 }
 
 EXPORT void orc_chain_schedule(const orc_chain *c, double *T0, double *Tf,
@@ -340,8 +363,17 @@ static int orc_accept(orc_chain *c, int64_t delta, uint64_t it) {
   double u = orc_uniform(c->seed, c->stream, it);
   double T = orc_sched_T(&c->S, it);
   double prod = T * log(u);
-  if (fabs((double)delta + prod) < 1e-9 * T) c->near_ties++;
+  if (fabs((double)delta + prod) < 1e-9 * T) {
+    if (c->nlog && c->near_ties < c->nlog_cap) c->nlog[c->near_ties] = it;
+    c->near_ties++;
+  }
   return (double)delta < -prod;
+}
+
+/* R3 for a given (delta, it) under the chain's schedule and random stream:
+ * 1 if the proposal is accepted.  Changes nothing but the near-tie count. */
+EXPORT int32_t orc_chain_accepts(orc_chain *c, int64_t delta, uint64_t it) {
+  return orc_accept(c, delta, it);
 }
 
 /* Step (d) of section 2.2 for the accepted swap (r, s) with cost change delta:
