@@ -1,15 +1,33 @@
 #!/usr/bin/env python
 """Benchmark: Delta-matrix simulated annealing for the QAP on GB300.
 
-One step = one whole single-chain SA run of the measured workload: set-up
-(B', Delta_0, C0 -- step (a) of section 2.2), I iterations of the window
-scan + Delta update (steps (b)-(e)), and the result.  With --gpus N (torchrun)
-every rank runs an independent replica of the chain on its own GPU (a single
-chain does not shard), so work per GPU is fixed ("scaling": "weak").
+Default workload (the largest single-GPU configuration): one chain on the
+N = 1024 structured instance -- B the Manhattan distances of a 32 x 32 grid, A
+symmetric with 30 % nonzeros in [1, 10] -- over the whole geometric schedule
+of I = 2e9 iterations (T0 = 0.5 mean|Delta0|, Tf = 1e-3 T0).  The K timed steps
+are K consecutive pieces of that one run (I / K iterations each, the last one
+takes the remainder), so the timed region is the whole schedule whatever K is.
+The set-up (B', Delta0, C0 -- step (a) of section 2.2) is inside the first
+step.  Warm-up steps run 1e6-iteration pieces of a separate chain of the same
+instance and schedule.
 
---impl reference times the CPU oracle (single thread) on a bounded sample of the
-same workload: the full schedule of the same instance at I/10 iterations (I/200
-for N = 256), which has the same acceptance rate a(I) as the full-length run.
+The same run gives both numbers:
+  value  iterations / device time (CUDA events on the chain's stream around
+         the set-up and every piece; inputs already in HBM);
+  e2e    iterations / host wall time of the same run through the public API,
+         including the host-to-device copy of A, B, p0 from pinned memory and a
+         device-to-host read of the result (p, cost, accepts) after every step.
+
+Extra fields of the same line: the N = 100 (I = 1e8) and N = 256 (I = 1e9)
+single-chain workloads, the 512-chain batch and a bounded serving sample, the
+microbenchmarked peaks of this GPU (qap_peaks_measure), and the roofline of
+the SA kernel by the method's algorithmic bytes.  With --gpus N (torchrun)
+every rank runs an independent replica (own Philox stream); a single chain
+does not shard, so work per GPU is fixed ("scaling": "weak").
+
+--impl reference times the CPU oracle (one thread) on a bounded sample of the
+same workload: consecutive 100-iteration pieces of the start of the same
+schedule on the same instance, one piece per step.
 """
 from __future__ import annotations
 
@@ -19,72 +37,91 @@ import multiprocessing as mp
 import os
 import statistics
 import subprocess
-import tempfile
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "n100": dict(N=100, I=10 ** 8, seed=1, cpu_div=10,
+    "c3": dict(kind="grid", side=32, N=1024, I=2 * 10 ** 9, seed=1,
+               desc="single chain, N=1024: B = Manhattan distances on a 32x32 grid, "
+                    "A symmetric with 30% nonzeros uniform int [1,10], random p0, "
+                    "geometric cooling T0=0.5*mean|Delta0|, Tf=1e-3*T0, I=2e9",
+               cpu_iters=2000, ref_piece=100),
+    "n100": dict(kind="uniform", N=100, I=10 ** 8, seed=1,
                  desc="single chain, N=100, A and B symmetric uniform int [0,99], "
                       "zero diagonal, random p0, geometric cooling "
                       "T0=0.5*mean|Delta0|, Tf=1e-3*T0, I=1e8",
-                 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of
-                 # sa_tier1_kernel<256> on this instance (2e6 iterations): the chain
-                 # state and the code are read once per launch and everything stays
-                 # on chip, so a launch of any length moves the same bytes
-                 dram_bytes_per_launch=489984,
-                 traffic_basis="ncu capture of one 2e6-iteration launch of the same "
-                               "kernel on this instance; independent of the launch's "
-                               "length (state on chip)"),
-    "n256": dict(N=256, I=10 ** 9, seed=1, cpu_div=200,
+                 cpu_iters=10 ** 7, ref_piece=10 ** 6),
+    "n256": dict(kind="uniform", N=256, I=10 ** 9, seed=1,
                  desc="single chain, N=256, A and B symmetric uniform int [0,99], "
                       "zero diagonal, random p0, geometric cooling "
-                      "T0=0.5*mean|Delta0|, Tf=1e-3*T0, I=1e9"),
+                      "T0=0.5*mean|Delta0|, Tf=1e-3*T0, I=1e9",
+                 cpu_iters=5 * 10 ** 6, ref_piece=2 * 10 ** 5),
     "batch512": dict(count=512, n_lo=20, n_hi=300, I=10 ** 7, seed=4,
                      desc="512 independent chains, N ~ U{20..300}, uniform symmetric "
                           "int [0,99] instances (seed 1000+c, Philox stream c), "
                           "I=1e7 each, one persistent graph-captured launch"),
-    "serve": dict(count=100, rates=(100, 1000, 5000), n_lo=30, n_hi=600,
+    "serve": dict(count=1000, rates=(100, 200, 500, 1000, 2000, 5000), n_lo=30, n_hi=600,
                   i_lo=1e6, i_hi=1e8, seed=5,
                   desc="Poisson solve requests, N log-uniform [30,600], I log-uniform "
                        "[1e6,1e8], uniform symmetric int [0,99] instances, continuous "
-                       "batching; a bounded sample of 100 requests per rate"),
+                       "batching"),
 }
-SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 bytes
+# The bounded serving sample reported beside the default workload.
+SERVE_SAMPLE = dict(count=200, rates=(1000,))
+WARMUP_PIECE = 10 ** 6
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="n100")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra single-chain, batch and serving fields")
     return ap.parse_args()
 
 
-# --------------------------------------------------------------------------- #
-# CPU oracle legs (only place bench.py touches oracle/)
-# --------------------------------------------------------------------------- #
-def _oracle_sample(N: int, I: int, seed: int, q):
-    import oracle
+def instance(wl):
     from paper_1208_2675_gb300 import instances
-    A, B, p0 = instances.taixxa_like(N, seed)
-    c = oracle.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=I, seed=seed)
+    if wl["kind"] == "grid":
+        return instances.grid_instance(wl["side"], wl["seed"])
+    return instances.taixxa_like(wl["N"], wl["seed"])
+
+
+def config_of(wl):
+    """The config dict both arms print (identical, so the lines compare)."""
+    return {"workload": wl["desc"], "N": wl["N"], "I": wl["I"], "chains_per_gpu": 1,
+            "schedule": "geometric, T0=0.5*mean|Delta0|, Tf=1e-3*T0",
+            "l2": "inputs and state on chip; the SA kernel moves no DRAM bytes per "
+                  "iteration (see roofline.traffic)"}
+
+
+# --------------------------------------------------------------------------- #
+# CPU oracle legs (the only places bench.py touches oracle/)
+# --------------------------------------------------------------------------- #
+def _oracle_prefix(wl, iters, q):
+    import oracle
+    A, B, p0 = instance(wl)
     t = time.perf_counter()
-    c.run(I)
+    c = oracle.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=wl["I"], seed=wl["seed"])
+    t_setup = time.perf_counter() - t
+    t = time.perf_counter()
+    c.run(iters)
     dt = time.perf_counter() - t
-    q.put((dt, c.state()["accepts"]))
+    q.put((t_setup, dt, c.state()["accepts"]))
 
 
-def oracle_sample_seconds(N: int, I: int, seed: int):
+def oracle_prefix_async(wl, iters):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    pr = ctx.Process(target=_oracle_sample, args=(N, I, seed, q))
+    pr = ctx.Process(target=_oracle_prefix, args=(wl, iters, q))
     pr.start()
     return pr, q
 
@@ -156,111 +193,191 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------- #
+# roofline of the SA kernel (the method's algorithmic bytes)
+# --------------------------------------------------------------------------- #
+def roofline(wl, info, accepts, t_kernel, peaks, sms_held):
+    """Bytes by the method's own count: an iteration reads one Delta cell
+    (4 B); an accepted swap reads and writes every one of the M cells (8 B) and
+    reads A and B' once for rows r,s (2 w B per cell, w = 1 for the int8 rows).
+    Peak: shared memory of the SMs the chain holds, at the measured bytes per
+    clock and SM clock of this GPU.  The kernel moves no DRAM bytes per
+    iteration: its state stays on chip."""
+    N, I = wl["N"], info["iterations"]
+    M = N * (N - 1) // 2
+    w = 1
+    algo = accepts * M * (8 + 2 * w) + 4 * I
+    achieved = algo / t_kernel / 1e9
+    per_sm = peaks["smem_bytes_per_clk_sm"] * peaks["sm_mhz"] * 1e6 / 1e9
+    peak = per_sm * sms_held
+    # what the kernel actually moved: a proposal evaluated directly reads rows
+    # r,s of A and B' (4N), a direct accept moves O(N) (6N), a proposal read
+    # from Delta is 4 B, an accept with Delta maintained is 8M + 2N^2
+    d_it, d_acc = info["direct_iters"], info["direct_accepts"]
+    moved = d_it * 4 * N + d_acc * 6 * N + (I - d_it) * 4 + (accepts - d_acc) * (8 * M + 2 * N * N)
+    nbar = 2  # hardware barriers per accepted swap (CTA or cluster)
+    bar_ns = (peaks["cta_barrier_ns"] if sms_held == 1
+              else max(v for v in peaks["cluster_barrier_ns"].values()))
+    per_acc_ns = t_kernel / max(accepts, 1) * 1e9
+    return {
+        "bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak, "traffic": None,
+        "algorithmic_bytes": algo,
+        "bytes_basis": "accepts*M*(8+2w) + 4*I, w=1 (int8 A and B' rows)",
+        "peak_basis": f"{sms_held} SM(s) x measured {peaks['smem_bytes_per_clk_sm']:.1f} B/clk "
+                      f"x measured {peaks['sm_mhz']:.0f} MHz (qap_peaks_measure)",
+        "frac_of_chip": achieved / (per_sm * peaks["sm_count"]),
+        "moved_bytes": moved, "moved_frac": moved / t_kernel / 1e9 / peak,
+        "latency": {"ns_per_accept": per_acc_ns,
+                    "barrier_floor_ns_per_accept": nbar * bar_ns,
+                    "frac_of_barrier_floor": nbar * bar_ns / per_acc_ns,
+                    "basis": "two hardware barriers per accepted swap at the measured "
+                             "barrier latency: the floor a chain of dependent accepts "
+                             "cannot go below"},
+    }
+
+
+# --------------------------------------------------------------------------- #
 # our arm
 # --------------------------------------------------------------------------- #
-def run_ours(args, rank: int, world: int, local_rank: int, dist):
+def pieces(I, K):
+    base = I // K
+    out = [base] * K
+    out[-1] += I - base * K
+    return out
+
+
+def run_chain_workload(args, wl, rank, world, dev, dist, peaks, timed=True):
+    """One whole run of a single-chain workload, in K pieces; returns a dict."""
     import torch
-    from paper_1208_2675_gb300 import instances, replicas, sa
-
-    wl = WORKLOADS[args.workload]
-    N, I, seed = wl["N"], wl["I"], wl["seed"]
-    M = N * (N - 1) // 2
-    dev = torch.device(f"cuda:{local_rank}")
-    torch.cuda.set_device(dev)
-    sa.lib()
-
-    # CPU oracle baseline (rank 0, N=1): started first, runs beside the GPU work.
-    cpu_proc = None
-    I_sample = I // wl["cpu_div"]
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_proc, cpu_q = oracle_sample_seconds(N, I_sample, seed)
-
-    A, B, p0 = instances.taixxa_like(N, seed)
-    stream_id = replicas.stream_id_for(rank)  # independent replicas
-    kw = dict(t0=0.5, tf=1e-3, total_iters=I, seed=seed, stream_id=stream_id)
-    At, Bt, pt = (torch.from_numpy(x).to(dev) for x in (A, B, p0))
-    p_out = torch.zeros(N, dtype=torch.int32, device=dev)
-    c_out = torch.zeros(1, dtype=torch.int64, device=dev)
-    a_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    from paper_1208_2675_gb300 import replicas, sa
+    A, B, p0 = instance(wl)
+    N, I = wl["N"], wl["I"]
+    stream_id = replicas.stream_id_for(rank)
+    kw = dict(t0=0.5, tf=1e-3, total_iters=I, seed=wl["seed"], stream_id=stream_id)
+    Ah, Bh, ph = (torch.from_numpy(x).pin_memory() for x in (A, B, p0))
+    At, Bt, pt = (torch.empty_like(x, device=dev) for x in (Ah, Bh, ph))
     stream = torch.cuda.Stream(dev)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
-    chunk = int(os.environ.get("QAPSA_CHUNK_ITERS", str(1 << 26)))
-    sa_launches = -(-I // chunk)
+    K = max(1, args.steps)
 
-    def step():
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        with torch.cuda.stream(stream):
-            flush.fill_(1)
-        ev[0].record(stream)
-        h = sa.Chain.from_device(At, Bt, pt, stream=stream.cuda_stream, **kw)
-        ev[1].record(stream)
-        h.run_async(I)
-        ev[2].record(stream)
-        sa.qap_sa_result_device(h.h, p_out.data_ptr(), c_out.data_ptr(), a_out.data_ptr())
-        ev[3].record(stream)
-        ev[3].synchronize()
-        h.sync()
-        acc = int(a_out.item())
-        info = h.info()
-        h.close()
-        return (ev[0].elapsed_time(ev[3]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3, acc,
-                info["direct_iters"], info["direct_accepts"])
-
-    for _ in range(args.warmup):
-        step()
+    # warm-up: 1e6-iteration pieces of a separate chain of the same schedule
+    with torch.cuda.stream(stream):
+        At.copy_(Ah)
+        Bt.copy_(Bh)
+        pt.copy_(ph)
+    stream.synchronize()
+    if args.warmup:
+        hw = sa.Chain.from_device(At, Bt, pt, stream=stream.cuda_stream, **kw)
+        for _ in range(args.warmup):
+            hw.run(min(WARMUP_PIECE, I // (args.warmup + 1)))
+        hw.close()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
-    clocks.start()
-    t_steps, t_sa, accs, dits, daccs = [], [], [], [], []
-    for _ in range(args.steps):
-        a, b, c, d, e = step()
-        t_steps.append(a)
-        t_sa.append(b)
-        accs.append(c)
-        dits.append(d)
-        daccs.append(e)
+
+    clocks = Clocks(dev.index or 0) if timed else None
+    if clocks:
+        clocks.start()
+    ev_set = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    results = []
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):  # host -> device copies of the inputs
+        At.copy_(Ah, non_blocking=True)
+        Bt.copy_(Bh, non_blocking=True)
+        pt.copy_(ph, non_blocking=True)
+    ev_set[0].record(stream)
+    h = sa.Chain.from_device(At, Bt, pt, stream=stream.cuda_stream, **kw)
+    ev_set[1].record(stream)
+    for k, n in enumerate(pieces(I, K)):
+        ev[k][0].record(stream)
+        h.run_async(n)
+        ev[k][1].record(stream)
+        results.append(h.result())  # device -> host read of the step's result
+    t1 = time.perf_counter()
     torch.cuda.synchronize()
-    clk = clocks.stop()
-    total = sum(t_steps)
-    total_max = replicas.max_over_ranks(total, dist, dev)
+    clk = clocks.stop() if clocks else None
+    h.sync()
+    info = h.info()
+    h.close()
+    t_setup = ev_set[0].elapsed_time(ev_set[1]) / 1e3
+    t_pieces = [e[0].elapsed_time(e[1]) / 1e3 for e in ev]
+    t_dev = t_setup + sum(t_pieces)
+    t_dev_max = replicas.max_over_ranks(t_dev, dist, dev)
+    t_e2e_max = replicas.max_over_ranks(t1 - t0, dist, dev)
+    p_fin, cost_fin, acc_fin = results[-1]
+    chunk = int(os.environ.get("QAPSA_CHUNK_ITERS", str(1 << 26)))
+    per_piece_launches = [-(-n // chunk) * (4 if info["tier"] == 2 else 1) for n in pieces(I, K)]
+    return {"N": N, "I": I, "t_dev": t_dev_max, "t_e2e": t_e2e_max, "t_setup": t_setup,
+            "t_kernel": sum(t_pieces), "t_pieces": t_pieces, "info": info,
+            "accepts": acc_fin, "cost": cost_fin, "clocks": clk,
+            "launches": 4 + sum(per_piece_launches),
+            "h2d": 2 * N * N * 4 + 4 * N, "d2h_per_step": 4 * N + 8 + 8}
 
-    # ---- end to end through the host-pointer API (pinned host buffers) ----
-    Ah = torch.from_numpy(A).pin_memory()
-    Bh = torch.from_numpy(B).pin_memory()
-    ph = torch.from_numpy(p0).pin_memory()
-    e2e_times = []
-    for k in range(max(1, min(args.steps, 3)) + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h = sa.Chain(Ah.numpy(), Bh.numpy(), ph.numpy(), **kw)
-        h.run(I)
-        p_res, cost_res, acc_res = h.result()
-        dt = time.perf_counter() - t0
-        h.close()
-        if k:  # first one warms the host path
-            e2e_times.append(dt)
-    e2e_value = I / statistics.median(e2e_times)
 
+def gpu_prefix_seconds(wl, iters, dev):
+    """The GPU on the same prefix of the schedule the CPU baseline runs."""
+    import torch
+    from paper_1208_2675_gb300 import sa
+    A, B, p0 = instance(wl)
+    At, Bt, pt = (torch.from_numpy(x).to(dev) for x in (A, B, p0))
+    stream = torch.cuda.Stream(dev)
+    kw = dict(t0=0.5, tf=1e-3, total_iters=wl["I"], seed=wl["seed"])
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    h = sa.Chain.from_device(At, Bt, pt, stream=stream.cuda_stream, **kw)
+    h.run(min(1000, iters))  # warm
+    h.close()
+    e[0].record(stream)
+    h = sa.Chain.from_device(At, Bt, pt, stream=stream.cuda_stream, **kw)
+    h.run_async(iters)
+    e[1].record(stream)
+    e[1].synchronize()
+    _, _, acc = h.result()
+    h.close()
+    return e[0].elapsed_time(e[1]) / 1e3, acc
+
+
+def run_ours(args, rank, world, local_rank, dist):
+    import torch
+    from paper_1208_2675_gb300 import sa
+    wl = WORKLOADS[args.workload]
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    sa.lib()
+    cpu_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_proc, cpu_q = oracle_prefix_async(wl, wl["cpu_iters"])
+    peaks = sa.qap_peaks_measure()
+    r = run_chain_workload(args, wl, rank, world, dev, dist, peaks)
+    info = r["info"]
+    sms_held = info["ctas"]
+    extras = {}
+    if not args.no_extras and args.workload == "c3":
+        for name in ("n100", "n256"):
+            sub = argparse.Namespace(**{**vars(args), "steps": 1, "warmup": 1})
+            x = run_chain_workload(sub, WORKLOADS[name], rank, world, dev, dist, peaks,
+                                   timed=False)
+            extras[name] = {"workload": WORKLOADS[name]["desc"],
+                            "iterations_per_sec": world * x["I"] / x["t_dev"],
+                            "e2e_iterations_per_sec": world * x["I"] / x["t_e2e"],
+                            "accept_rate": x["accepts"] / x["I"],
+                            "s_per_run": x["t_dev"],
+                            "roofline": roofline(WORKLOADS[name], x["info"], x["accepts"],
+                                                 x["t_kernel"], peaks, 1)}
+        extras["batch512"] = batch_fields(rank, world, dev, dist, steps=1, warmup=1)
+        if rank == 0:
+            extras["serve_sample"] = serve_sweep(SERVE_SAMPLE["count"], SERVE_SAMPLE["rates"],
+                                                 dev)
     if rank != 0:
         return
-    acc_mean = statistics.mean(accs)
-    per_step = total_max / args.steps
-    value = world * args.steps * I / total_max
-    # roofline of sa_tier1_kernel: algorithmic shared-memory bytes of the work
-    # done in a step -- a proposal evaluated directly reads rows r,s of A and B'
-    # (4N), a directly handled accept moves O(N) (6N: rows r,s read, B' swapped),
-    # a proposal read from Delta is 4 bytes, an accept with Delta maintained
-    # reads and writes every cell (8M) and reads A and B' once (2N^2)
-    d_it, d_acc = statistics.mean(dits), statistics.mean(daccs)
-    bytes_step = (d_it * 4 * N + d_acc * 6 * N + (I - d_it) * 4 +
-                  (acc_mean - d_acc) * (8 * M + 2 * N * N))
-    t_kernel = statistics.mean(t_sa)
-    achieved = bytes_step / t_kernel / 1e9
-    mhz = clk.get("sm_mhz") or 2070.0
-    peak = SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6 / 1e9  # one SM
-    traffic = wl.get("dram_bytes_per_launch")
+    I, N = wl["I"], wl["N"]
+    value = world * I / r["t_dev"]
+    acc = r["accepts"]
+    rl = roofline(wl, info, acc, r["t_kernel"], peaks, sms_held)
+    traffic = PROFILED_TRAFFIC.get(args.workload)
+    if traffic:
+        rl["traffic"] = traffic["bytes_per_launch"]
+        rl["traffic_basis"] = traffic["basis"]
+    M = N * (N - 1) // 2
     line = {
         "metric": "sa_iterations_per_sec",
         "value": value,
@@ -268,79 +385,101 @@ def run_ours(args, rank: int, world: int, local_rank: int, dist):
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": per_step * 1e3,
+        "ms_per_step": r["t_dev"] / max(1, args.steps) * 1e3,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "int32",
-        "data": "synthetic (seeded Taixxa-like instance)",
-        "config": {"workload": wl["desc"], "N": N, "I": I, "chains_per_gpu": 1,
-                   "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{world}"},
-        "delta_cell_updates_per_sec": world * acc_mean * M / per_step,
-        "accept_rate": acc_mean / I,
-        "direct_mode": {"iterations": d_it, "accepts": d_acc,
-                        "note": "proposals evaluated directly while acceptance was high; "
-                                "Delta maintained for the rest"},
-        "sa_kernel_s_per_step": t_kernel,
-        "e2e": {"value": e2e_value, "unit": "iter/s",
-                "h2d_bytes_per_step": 2 * N * N * 4 + 4 * N,
-                "d2h_bytes_per_step": 4 * N + 8 + 8},
-        "gpu_launches": args.steps * (4 + sa_launches),
-        "roofline": {"bound": "smem", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "traffic_basis": wl.get("traffic_basis"),
-                     "peak_basis": "one SM: 128 B/clk x median SM clock under load "
-                                   "(derived; the kernel runs on one CTA)",
-                     "frac_of_chip": achieved / (peak * 152)},
-        "clocks": clk,
+        "data": "synthetic (seeded instance of the configuration's family)",
+        "config": config_of(wl),
+        "steps_are": f"{args.steps} consecutive pieces of one whole run of I={I} "
+                     "(set-up inside the first); warm-up: 1e6-iteration pieces of a "
+                     "separate chain",
+        "accept_rate": acc / I,
+        "accepts": acc,
+        "final_cost": r["cost"],
+        "delta_cell_updates_per_sec": world * (acc - info["direct_accepts"]) * M / r["t_dev"],
+        "direct_proposals_per_sec": world * info["direct_iters"] / r["t_dev"],
+        "modes": {"direct_iters": info["direct_iters"], "direct_accepts": info["direct_accepts"],
+                  "delta_iters": I - info["direct_iters"],
+                  "delta_accepts": acc - info["direct_accepts"], "tier": info["tier"],
+                  "sms_held": sms_held},
+        "sa_kernel_s": r["t_kernel"],
+        "setup_s": r["t_setup"],
+        "e2e": {"value": world * I / r["t_e2e"], "unit": "iter/s",
+                "h2d_bytes_per_step": r["h2d"] / max(1, args.steps),
+                "d2h_bytes_per_step": r["d2h_per_step"],
+                "basis": "host wall time of the same run: pinned host->device copy of "
+                         "A, B, p0 before the set-up, qap_sa_result after every step"},
+        "gpu_launches": r["launches"],
+        "roofline": rl,
+        "peaks": peaks,
+        "clocks": r["clocks"],
     }
+    line.update(extras)
     if cpu_proc is not None:
         cpu_proc.join()
-        dt, acc_cpu = cpu_q.get()
+        t_setup_cpu, dt, acc_cpu = cpu_q.get()
+        n = wl["cpu_iters"]
+        t_gpu, acc_gpu = gpu_prefix_seconds(wl, n, dev)
+        per_acc = dt / max(acc_cpu, 1)
         line["cpu_baseline"] = {
-            "value": I_sample / dt, "unit": "iter/s", "cores": 1, "kind": "oracle",
-            "sample": f"full schedule of the same N={N} instance at I={I_sample} "
-                      f"(a(I)={acc_cpu / I_sample:.4f} vs {acc_mean / I:.4f} at I={I}); "
-                      f"{dt:.1f} s on {cpu_model()}"}
+            "value": n / dt, "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"iterations 0..{n - 1} of the same schedule on the same instance "
+                      f"({acc_cpu} accepted swaps, a={acc_cpu / n:.3f}); {dt:.1f} s on "
+                      f"{cpu_model()}; set-up {t_setup_cpu:.1f} s not included",
+            "gpu_same_sample": {"value": n / t_gpu, "unit": "iter/s", "accepts": acc_gpu,
+                                "note": "set-up included"},
+            "oracle_whole_run_estimate_s": per_acc * acc,
+        }
     print(json.dumps(line), flush=True)
+
+
+# DRAM bytes of one launch of the SA kernel from an ncu capture (null until
+# captured for the current kernel).
+PROFILED_TRAFFIC = {}
 
 
 # --------------------------------------------------------------------------- #
 # reference arm: the CPU oracle
 # --------------------------------------------------------------------------- #
-def run_reference(args, rank: int, world: int):
+def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    from paper_1208_2675_gb300 import instances
     wl = WORKLOADS[args.workload]
-    N, seed = wl["N"], wl["seed"]
-    I = wl["I"] // wl.get("cpu_div", 10)
-    A, B, p0 = instances.taixxa_like(N, seed)
-
-    def step():
-        c = oracle.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=I, seed=seed)
-        t = time.perf_counter()
-        c.run(I)
-        return time.perf_counter() - t
-
+    if "N" not in wl:
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the reference arm times single-chain workloads"}))
+        return
+    A, B, p0 = instance(wl)
+    piece = wl["ref_piece"]
+    c = oracle.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=wl["I"], seed=wl["seed"])
     for _ in range(args.warmup):
-        step()
-    ts = [step() for _ in range(args.steps)]
+        c.run(piece)
+    a0 = c.state()["accepts"]
+    ts = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        c.run(piece)
+        ts.append(time.perf_counter() - t)
     total = sum(ts)
-    value = args.steps * I / total
+    acc = c.state()["accepts"] - a0
+    value = args.steps * piece / total
+    start = args.warmup * piece
+    sample = (f"iterations {start}..{start + args.steps * piece - 1} of the same schedule "
+              f"on the same instance, {piece} per step ({acc} accepted swaps); one thread "
+              f"on {cpu_model()}")
     line = {
         "metric": "sa_iterations_per_sec", "value": value, "unit": "iter/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "ms_per_step": total / max(1, args.steps) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic (seeded Taixxa-like instance)",
-        "config": {"workload": wl["desc"], "N": N, "I": wl["I"], "chains_per_gpu": 1,
-                   "parallelism": "single CPU thread"},
+        "data": "synthetic (seeded instance of the configuration's family)",
+        "config": config_of(wl),
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                         "sample": f"full schedule of the same instance at I={I} per step"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -361,15 +500,34 @@ def _batch_problems(wl):
     return probs
 
 
-def run_batch(args, rank, world, local_rank, dist):
-    import torch
+def _oracle_one_chain(job):
+    sys.path.insert(0, ROOT)
+    import oracle
+    A, B, p0, kw, I = job
+    c = oracle.Chain(A, B, p0, **kw)
+    c.run(I)
+    return c.state()["accepts"]
+
+
+def _oracle_batch_chains(probs, I, q):
+    """Whole oracle runs of the given chains, one worker process per core."""
+    import concurrent.futures as cf
+    jobs = [(pr["A"], pr["B"], pr["p0"], dict(t0=0.5, tf=1e-3, total_iters=I,
+             seed=pr["seed"], stream=pr["stream_id"]), I) for pr in probs]
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=min(cores, len(jobs)),
+                                mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_one_chain, jobs))
+    q.put((time.perf_counter() - t, min(cores, len(jobs))))
+
+
+def batch_fields(rank, world, dev, dist, steps=1, warmup=1):
+    import torch  # noqa: F401
     from paper_1208_2675_gb300 import replicas, sa
     wl = WORKLOADS["batch512"]
-    dev = torch.device(f"cuda:{local_rank}")
-    torch.cuda.set_device(dev)
     all_probs = _batch_problems(wl)
     I = wl["I"]
-    # replicas: this rank's share of the chains, balanced by estimated work
     parts = replicas.partition_by_cost(
         [replicas.chain_cost(len(pr["p0"]), I) for pr in all_probs], world)
     probs = [all_probs[i] for i in parts[rank]]
@@ -384,19 +542,16 @@ def run_batch(args, rank, world, local_rank, dist):
         sa.qap_batch_destroy(b)
         return t2 - t0, t2 - t1, acc
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     if dist:
         dist.barrier()
-    clocks = Clocks(local_rank)
-    clocks.start()
-    res = [step() for _ in range(args.steps)]
-    clk = clocks.stop()
+    res = [step() for _ in range(steps)]
     t_step = replicas.max_over_ranks(statistics.mean(r[0] for r in res), dist, dev)
     t_run = replicas.max_over_ranks(statistics.mean(r[1] for r in res), dist, dev)
-    # the plain single-chain path on the same GPU: chains one after another
+    # the plain single-chain path on the same GPU: the largest chains one after another
     single = []
-    for pr in probs[:6]:
+    for pr in sorted(probs, key=lambda x: -len(x["p0"]))[:4]:
         h = sa.Chain(pr["A"], pr["B"], pr["p0"], t0=0.5, tf=1e-3, total_iters=I,
                      seed=pr["seed"], stream_id=pr["stream_id"])
         t = time.perf_counter()
@@ -404,45 +559,71 @@ def run_batch(args, rank, world, local_rank, dist):
         single.append((time.perf_counter() - t, len(pr["p0"])))
         h.close()
     n = len(all_probs)
-    per_chain = statistics.mean(t for t, _ in single)
+    out = {"workload": wl["desc"], "chains_per_sec": n / t_step, "unit": "chains/s",
+           "run_only_chains_per_sec": n / t_run, "iterations_per_sec": n * I / t_step,
+           "accept_rate": statistics.mean(r[2] for r in res) / (len(probs) * I),
+           "single_chain_path": {"chains_per_sec": len(single) / sum(t for t, _ in single),
+                                 "sample": f"the {len(single)} largest chains run one after "
+                                           f"another with qap_sa_run (N = "
+                                           f"{[m for _, m in single]})"}}
+    return out
+
+
+def run_batch(args, rank, world, local_rank, dist):
+    import torch
+    from paper_1208_2675_gb300 import sa
+    wl = WORKLOADS["batch512"]
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    sa.lib()
+    cpu_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        ctx = mp.get_context("spawn")
+        cpu_q = ctx.Queue()
+        sample = _batch_problems(wl)[:32]
+        cpu_proc = ctx.Process(target=_oracle_batch_chains, args=(sample, wl["I"], cpu_q))
+        cpu_proc.start()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    f = batch_fields(rank, world, dev, dist, steps=args.steps, warmup=args.warmup)
+    clk = clocks.stop()
+    if rank != 0:
+        return
     line = {
-        "metric": "batched_chains_per_sec", "value": n / t_step, "unit": "chains/s",
+        "metric": "batched_chains_per_sec", "value": f["chains_per_sec"], "unit": "chains/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded Taixxa-like instances)",
-        "config": {"workload": wl["desc"], "chains": n, "I": I,
-                   "sizes": "N ~ U{20..300}", "parallelism": f"replicas x{world}"},
-        "run_only_chains_per_sec": n / t_run,
-        "iterations_per_sec": n * I / t_step,
-        "accept_rate": statistics.mean(r[2] for r in res) / (len(probs) * I),
-        "single_chain_path": {"chains_per_sec": 1.0 / per_chain,
-                              "sample": f"first {len(single)} chains run one after another "
-                                        f"with qap_sa_run (N = {[m for _, m in single]})"},
+        "ms_per_step": len(_batch_problems(wl)) / f["chains_per_sec"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded Taixxa-like instances)",
+        "config": {"workload": wl["desc"], "chains": wl["count"], "I": wl["I"]},
+        **{k: v for k, v in f.items() if k not in ("chains_per_sec", "unit", "workload")},
         "clocks": clk,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    if cpu_proc is not None:
+        cpu_proc.join()
+        dt, cores = cpu_q.get()
+        line["cpu_baseline"] = {"value": 32 / dt, "unit": "chains/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"chains 0..31 of the same batch, whole runs, one "
+                                          f"process per core ({dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- #
 # serving: Poisson request streams through the continuous-batching server
 # --------------------------------------------------------------------------- #
-def run_serve(args, rank, world, local_rank):
-    if rank != 0:  # the serving sample runs on one GPU
-        return
+def serve_sweep(count, rates, dev):
     import numpy as np
-    import torch
     from paper_1208_2675_gb300 import instances, sa
     wl = WORKLOADS["serve"]
-    dev = torch.device(f"cuda:{local_rank}")
-    torch.cuda.set_device(dev)
-    sa.lib()
     out = []
-    for rate in wl["rates"]:
-        arrival, Ns, Is = instances.request_mix(wl["count"], rate, wl["n_lo"], wl["n_hi"],
+    for rate in rates:
+        arrival, Ns, Is = instances.request_mix(count, rate, wl["n_lo"], wl["n_hi"],
                                                 wl["i_lo"], wl["i_hi"], wl["seed"] + rate)
         reqs = []
-        for k in range(wl["count"]):
+        for k in range(count):
             A, B, p0 = instances.taixxa_like(int(Ns[k]), 7000 + k)
             reqs.append(dict(A=A, B=B, p0=p0, t0=0.5, tf=1e-3, total_iters=int(Is[k]),
                              stream_id=k, seed=7000 + k))
@@ -469,18 +650,35 @@ def run_serve(args, rank, world, local_rank):
                     "p50_latency_s": float(np.percentile(lat, 50)),
                     "p99_latency_s": float(np.percentile(lat, 99)),
                     "p50_queue_s": float(np.percentile(qs, 50)),
+                    "p99_queue_s": float(np.percentile(qs, 99)),
                     "completed_iterations_per_sec": float(sum(Is) / (t_end - t_start)),
                     "max_concurrent_requests": maxrun,
                     "wall_s": t_end - t_start})
+    return out
+
+
+def run_serve(args, rank, world, local_rank):
+    if rank != 0:  # the serving sweep runs on one GPU
+        return
+    import torch
+    from paper_1208_2675_gb300 import sa
+    wl = WORKLOADS["serve"]
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    sa.lib()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    out = serve_sweep(wl["count"], wl["rates"], dev)
+    clk = clocks.stop()
     line = {
         "metric": "serve_p99_latency_s", "value": out[-1]["p99_latency_s"], "unit": "s",
         "n_gpus": world, "steps": 1, "warmup": 0, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded Taixxa-like instances, Poisson arrivals)",
-        "config": {"workload": wl["desc"]}, "sweep": out,
+        "config": {"workload": wl["desc"], "requests_per_rate": wl["count"]},
+        "sweep": out, "clocks": clk,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    print(json.dumps(line), flush=True)
 
 
 def main():

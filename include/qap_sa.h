@@ -153,6 +153,8 @@ typedef struct qap_sa_info {
   uint64_t warp_iters;    /* direct iterations run by one warp alone, with no
                              block barrier (while the acceptance rate is
                              above 1/512, or 1/64 for N above ~180)        */
+  int32_t ctas;           /* CTAs (= SMs) the chain holds while it runs     */
+  int32_t threads;        /* threads per CTA of the SA kernel               */
 } qap_sa_info;
 QAP_EXPORT int qap_sa_get_info(qap_sa *h, qap_sa_info *out);
 
@@ -162,6 +164,35 @@ QAP_EXPORT int qap_sa_delta(qap_sa *h, int32_t *delta_out);
 
 /* T(it) of the handle's schedule as a binary64 (see qap_schedule).          */
 QAP_EXPORT double qap_sa_temperature(const qap_sa *h, uint64_t it);
+
+/* Near-ties of the handle (after a stream sync): the test of Eq. (2) is
+ * decided in binary64 with CUDA's log, and a test with
+ * |delta + T ln u| < 1e-9 T is a near-tie, where another libm's log could decide
+ * it the other way.  Writes the iteration indices of the first
+ * min(cap, 8) near-ties to it_out (host, cap uint64) and their total count to
+ * *count (may be NULL).  QAP_E_INVAL if h is NULL, cap < 0, or cap > 0 with
+ * it_out NULL.                                                              */
+QAP_EXPORT int qap_sa_near_tie_log(qap_sa *h, uint64_t *it_out, int32_t cap,
+                                   uint64_t *count);
+
+/* Eq. (2) (section 2.1) for given proposals, decided exactly as the SA kernels
+ * decide it inside a window (section 3 (ii)), with the handle's schedule and
+ * random stream: probe k is the proposal of iteration it[k] with swap cost
+ * delta[k] in a window that starts at iteration it0[k].  For a diagnostic of
+ * the binary32 pre-test against the binary64 rule; it changes no state.
+ *   it, it0, delta : host, n entries each; it0[k] <= it[k] < it0[k] + 2^30
+ *   out            : host, n int32: bit 0 the decision (1 = accept); bits 2-3
+ *                    the binary32 interval of the prepared per-window tables
+ *                    (0 reject, 1 accept, 2 undecided -> binary64); bits 4-5
+ *                    the interval of the in-window pre-test; bit 6 set when
+ *                    the integer pre-filter of a window of it - it0 + 1
+ *                    proposals rejects; bit 7 set when the binary64 test saw
+ *                    a near-tie
+ * Blocks until done.  QAP_E_INVAL for NULL arguments or n < 0, QAP_E_RANGE for
+ * an offset outside [0, 2^30).                                              */
+QAP_EXPORT int qap_sa_accept_probe(qap_sa *h, int32_t n, const uint64_t *it,
+                                   const uint64_t *it0, const int32_t *delta,
+                                   int32_t *out);
 
 /* Frees every resource of the handle (NULL is ignored).                     */
 QAP_EXPORT void qap_sa_destroy(qap_sa *h);
@@ -261,8 +292,10 @@ QAP_EXPORT int qap_server_stop(qap_server *s);
  * same input defects as qap_sa_create; in that case the outputs hold
  * unspecified values.  The first call on a device looks up the array's device
  * address (with that device current); make that first call before any stream
- * capture.  All calls share the one array, so calls that overlap on the GPU
- * (from several threads or streams) race: serialise them.                    */
+ * capture.  The address is kept for the life of the process: after a
+ * cudaDeviceReset it is stale, and this entry point must not be called again
+ * on that device.  All calls share the one array, so calls that overlap on the
+ * GPU (from several threads or streams) race: serialise them.                */
 #define QAP_NOALLOC_MAX_N 256
 QAP_EXPORT int qap_sa_setup_noalloc(const int32_t *A, const int32_t *B, int32_t N,
                                     const int32_t *p, int32_t *delta_out,

@@ -47,6 +47,10 @@ unsigned long long chunk_iters() {
   return v;
 }
 
+// Set once by preload_kernels (see there).
+int g_tmem_min_smem = 0;   // least dynamic shared memory of a TMEM-kernel launch
+bool g_tmem_ok = true;     // one TMEM-holding CTA per SM is guaranteed
+
 int device_smem_optin() {
   int dev = 0, v = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -59,11 +63,7 @@ int device_smem_optin() {
 // Row stride of the int8 A and B' rows: 16 bytes times an odd number, so that
 // eight threads reading 16-byte chunks of eight consecutive rows hit distinct
 // bank groups.
-int row_stride(int N) {
-  int c = (N + 15) / 16;
-  if ((c & 1) == 0) ++c;
-  return 16 * c;
-}
+constexpr int row_stride(int N) { return 16 * (((N + 15) / 16) | 1); }
 
 // Height of the register tiles of Delta.
 int tile_rows(int) { return kT1R; }
@@ -123,6 +123,47 @@ double schedule_T(const Schedule &S, unsigned long long it) {
 }
 
 }  // namespace
+
+// Largest window offset the probe accepts (windows are at most M < 2^31 long).
+constexpr unsigned long long kProbeMaxOffset = 1ull << 30;
+
+// Eq. (2) for given proposals, decided as the SA kernels decide it, for tests of
+// the binary32 pre-test against binary64.  Probe k is the proposal of iteration
+// it[k] with swap cost delta[k], in a window that starts at it0[k] <= it[k].
+// out[k] bit 0: the decision (binary32 interval, binary64 when undecided);
+// bits 2-3: the interval of the prepared tables (0 reject, 1 accept,
+// 2 undecided); bits 4-5: the interval of the in-window pre-test; bit 6: the
+// integer pre-filter of a window of it[k] - it0[k] + 1 proposals rejects;
+// bit 7: the binary64 test saw a near-tie.
+__global__ void accept_probe_kernel(ChainDev g, int n, const unsigned long long *its,
+                                    const unsigned long long *it0s, const int *deltas,
+                                    int *out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const unsigned long long it = its[k], it0 = it0s[k];
+  const int dv = deltas[k];
+  const int j = (int)(it - it0);
+  // the prepared tables: the Philox block of it, T of the block's first iteration
+  const unsigned long long q = it >> 2;
+  const int w = (int)(it & 3u);
+  const uint4 x = rng_block(g.seed, g.stream, q);
+  const float Tq = g.T0f * exp2f(u64_to_f32(q << 2) * g.log2a_f);
+  const float2 bt = accept_interval(g.mrel, Tq * exp2f((float)w * g.log2a_f), word_of(x, w));
+  const float df = (float)dv;
+  const int dt = dv <= 0 ? 1 : (df < bt.x ? 1 : (!(df > bt.y) ? 2 : 0));
+  // the in-window pre-test and the integer pre-filter of a window [it0, it]
+  const float Tw = g.T0f * exp2f(u64_to_f32(it0) * g.log2a_f);
+  const unsigned o = pretest_cells(g.seed, g.stream, g.log2a_f, g.mrel, it0, Tw, j, 0, 0, 0,
+                                   dv, 0, 0, 0, 1u);
+  const int dw = dv <= 0 ? 1 : ((o & 1u) ? 1 : (((o >> 4) & 1u) ? 2 : 0));
+  const float Te = Tw * exp2f((float)(j + 1) * g.log2a_f);
+  const float tmax = fmaxf(Tw, Te) * 24.5f;
+  const int thr = (tmax < 1.0e9f) ? (int)ceilf(tmax) + 1 : 0x7FFFFFFF;
+  const int filt = dv > thr ? 1 : 0;
+  unsigned long long nt = 0;
+  const int ex = dv <= 0 ? 1 : exact_accept(g.seed, g.stream, g.T0, g.P, dv, it, &nt, nullptr);
+  out[k] = ex | (dt << 2) | (dw << 4) | (filt << 6) | ((nt ? 1 : 0) << 7);
+}
 
 struct qap_sa {
   int N = 0, S = 0, M = 0;
@@ -232,8 +273,47 @@ void preload_kernels() {
     cudaFuncSetAttribute(sa_tier2_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
                          1);
     cudaGetLastError();
+    // The kernels that keep Delta in Tensor Memory allocate all 512 columns of
+    // the SM's TMEM; a second such CTA on the same SM would wait in
+    // tcgen05.alloc for the first to finish -- across the CTAs of a cluster,
+    // which wait for each other at cluster barriers, that could never end.
+    // Their register use at 640 threads keeps one CTA per SM; check it, and
+    // where it does not hold, make every launch of them ask for more than half
+    // of the SM's shared memory, which does.
+    const void *tmem_kernels[4] = {(const void *)sa_tier1_kernel<kT1LargeThreads>,
+                                   (const void *)sa_batch_kernel,
+                                   (const void *)sa_tier2_kernel,
+                                   (const void *)sa_tier2_batch_kernel};
+    int dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    auto ctas_per_sm = [](const void *k, int smem_dyn) {
+      int n = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kT1LargeThreads, smem_dyn) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+      }
+      return n;
+    };
+    bool one = true;
+    for (const void *k : tmem_kernels) one = one && ctas_per_sm(k, 0) <= 1;
+    if (!one) {
+      g_tmem_min_smem = per_sm / 2 + 1;
+      for (const void *k : tmem_kernels) {
+        cudaFuncAttributes fa;
+        const int dyn = (cudaFuncGetAttributes(&fa, k) == cudaSuccess)
+                            ? g_tmem_min_smem - (int)fa.sharedSizeBytes : g_tmem_min_smem;
+        if (ctas_per_sm(k, dyn > 0 ? dyn : 0) > 1) g_tmem_ok = false;
+      }
+    }
+    cudaGetLastError();
   });
 }
+
+// Dynamic shared memory of a launch of a TMEM-holding kernel: at least what
+// keeps it alone on its SM.
+int tmem_smem(int want) { return want > g_tmem_min_smem ? want : g_tmem_min_smem; }
 
 int tier2_cluster(int N) {
   const int nt = (int)make_tiles(N, kT2R).size();
@@ -472,6 +552,10 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   }
   h->layout = t1_layout(N, S);
   h->smem_bytes = h->tier == 1 ? h->layout.bytes : tier2_bytes(N, h->cluster);
+  if (h->tier == 2 || h->nthreads > kT1SmallThreads) {
+    if (!g_tmem_ok) return fail(QAP_E_UNSUPPORTED);
+    h->smem_bytes = tmem_smem(h->smem_bytes);
+  }
   CKF(cudaStreamSynchronize(stream));
   *out = h;
   return rc;
@@ -594,7 +678,7 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
           <<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
     } else {
       sa_tier1_kernel<kT1LargeThreads>
-          <<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
+          <<<1, h->nthreads, h->smem_bytes, h->stream>>>(h->dev, stop);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "sa_tier1_kernel launch");
@@ -671,6 +755,8 @@ int qap_sa_get_info(qap_sa *h, qap_sa_info *out) {
   out->direct_iters = st.direct_iters;
   out->direct_accepts = st.direct_accepts;
   out->warp_iters = st.warp_iters;
+  out->ctas = h->cluster;
+  out->threads = h->nthreads;
   return st.error ? QAP_E_STATE : QAP_OK;
 }
 
@@ -685,6 +771,50 @@ int qap_sa_delta(qap_sa *h, int32_t *delta_out) {
 double qap_sa_temperature(const qap_sa *h, uint64_t it) {
   if (!h) return 0.0;
   return schedule_T(h->sched, it);
+}
+
+int qap_sa_near_tie_log(qap_sa *h, uint64_t *it_out, int32_t cap, uint64_t *count) {
+  if (!h || cap < 0 || (cap > 0 && !it_out)) return QAP_E_INVAL;
+  ChainStatus st{};
+  CK(cudaMemcpyAsync(&st, h->st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int n = (int)std::min<unsigned>(st.near_log_n, (unsigned)kNearLog);
+  for (int k = 0; k < n && k < cap; ++k) it_out[k] = st.near_log[k];
+  if (count) *count = st.near_ties;
+  return QAP_OK;
+}
+
+int qap_sa_accept_probe(qap_sa *h, int32_t n, const uint64_t *it, const uint64_t *it0,
+                        const int32_t *delta, int32_t *out) {
+  if (!h || n < 0 || (n > 0 && (!it || !it0 || !delta || !out))) return QAP_E_INVAL;
+  if (n == 0) return QAP_OK;
+  for (int32_t k = 0; k < n; ++k)
+    if (it0[k] > it[k] || it[k] - it0[k] >= (uint64_t)kProbeMaxOffset) return QAP_E_RANGE;
+  cudaStream_t st = h->stream;
+  unsigned long long *d_it = nullptr, *d_it0 = nullptr;
+  int *d_delta = nullptr, *d_out = nullptr;
+  auto cleanup = [&]() {
+    dfree(d_it, st);
+    dfree(d_it0, st);
+    dfree(d_delta, st);
+    dfree(d_out, st);
+  };
+  cudaError_t e = cudaMallocAsync((void **)&d_it, sizeof(uint64_t) * n, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_it0, sizeof(uint64_t) * n, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_delta, sizeof(int32_t) * n, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_out, sizeof(int32_t) * n, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_it, it, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_it0, it0, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_delta, delta, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    accept_probe_kernel<<<(n + 127) / 128, 128, 0, st>>>(h->dev, n, d_it, d_it0, d_delta, d_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "qap_sa_accept_probe");
+  return QAP_OK;
 }
 
 void qap_sa_destroy(qap_sa *h) { free_handle(h); }
@@ -836,6 +966,12 @@ int qap_batch_create(const qap_problem *probs, int32_t count, qap_batch **out) {
   // The whole run is one graph: reset the work counters, then two persistent
   // launches side by side -- one CTA per chain for chains that fit one SM,
   // clusters for the others.
+  if (!g_tmem_ok) {
+    free_batch(b);
+    return QAP_E_UNSUPPORTED;
+  }
+  if (b->n1) b->smem = tmem_smem(b->smem);
+  if (b->n2) b->smem2 = tmem_smem(b->smem2);
   cudaGraph_t graph = nullptr;
   if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     return fail(e, "cudaStreamBeginCapture");
@@ -931,10 +1067,15 @@ void qap_batch_destroy(qap_batch *b) { free_batch(b); }
 // ------------------------------------------------------------------------- //
 namespace {
 
-constexpr int kNoAllocMaxN = 256;
+constexpr int kNoAllocMaxN = QAP_NOALLOC_MAX_N;
 constexpr size_t kNoAllocAlign = 256;
 constexpr size_t na_round(size_t x) { return (x + kNoAllocAlign - 1) / kNoAllocAlign * kNoAllocAlign; }
-constexpr size_t kNaRow = 272;  // row_stride(kNoAllocMaxN)
+// The row stride of the largest N: every N <= kNoAllocMaxN has a stride no
+// larger than this (row_stride is monotone), so its rows fit the array.
+constexpr size_t kNaRow = (size_t)row_stride(kNoAllocMaxN);
+static_assert(row_stride(kNoAllocMaxN - 1) <= row_stride(kNoAllocMaxN) &&
+                  row_stride(kNoAllocMaxN) >= kNoAllocMaxN,
+              "row stride of the allocation-free set-up");
 constexpr size_t kNaA = 0;
 constexpr size_t kNaB = kNaA + na_round((size_t)kNoAllocMaxN * kNaRow);
 constexpr size_t kNaG = kNaB + na_round((size_t)kNoAllocMaxN * kNaRow);
@@ -982,6 +1123,7 @@ extern "C" int qap_sa_setup_noalloc(const int32_t *A, const int32_t *B,
   if (rc) return rc;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   const int S = row_stride(N);
+  if ((size_t)S > kNaRow) return QAP_E_RANGE;  // cannot happen for N <= kNoAllocMaxN
   int8_t *A8 = reinterpret_cast<int8_t *>(base + kNaA);
   int8_t *Bp8 = reinterpret_cast<int8_t *>(base + kNaB);
   int *G = reinterpret_cast<int *>(base + kNaG);

@@ -19,6 +19,8 @@
 namespace qapsa {
 
 constexpr unsigned kNone = 0xFFFFFFFFu;
+// Near-ties whose iteration index a chain keeps (the count is kept in full).
+constexpr int kNearLog = 8;
 
 // Per-chain counters kept in global memory between launches.
 struct ChainStatus {
@@ -36,6 +38,9 @@ struct ChainStatus {
   int need_rebuild;                   // Delta in global memory is stale (cluster
                                       // tier after direct mode): rebuild it
   int pad_;
+  unsigned long long near_log[kNearLog];  // iterations of the first near-ties
+  unsigned near_log_n;                    // near-ties logged (may exceed kNearLog)
+  unsigned pad2_;
 };
 
 // Everything one chain's kernels need (passed by value).
@@ -107,18 +112,28 @@ __device__ __forceinline__ double temperature(double T0, const double *P,
   return T;
 }
 
-// Eq. (2) decided in binary64 for a proposal with delta > 0.
+// Eq. (2) decided in binary64 for a proposal with delta > 0.  A near-tie
+// (|delta + T ln u| < 1e-9 T, where CUDA's and another libm's log could decide
+// differently) is counted in *near_ties and, if log is not NULL, its iteration
+// is recorded in nlog->near_log (one thread per chain passes nlog).
 __device__ __noinline__ int exact_accept(unsigned long long seed,
                                          unsigned stream, double T0,
                                          const double *P, int delta,
                                          unsigned long long it,
-                                         unsigned long long *near_ties) {
+                                         unsigned long long *near_ties,
+                                         ChainStatus *nlog) {
   const uint4 x = rng_block(seed, stream, it >> 2);
   const unsigned xi = word_of(x, (int)(it & 3u));
   const double u = __dmul_rn(__dadd_rn((double)xi, 0.5), 0x1p-32);
   const double T = temperature(T0, P, it);
   const double prod = __dmul_rn(T, log(u));
-  if (fabs(__dadd_rn((double)delta, prod)) < __dmul_rn(1e-9, T)) ++*near_ties;
+  if (fabs(__dadd_rn((double)delta, prod)) < __dmul_rn(1e-9, T)) {
+    ++*near_ties;
+    if (nlog) {
+      const unsigned k = nlog->near_log_n++;
+      if (k < (unsigned)kNearLog) nlog->near_log[k] = it;
+    }
+  }
   return (double)delta < -prod;
 }
 

@@ -268,7 +268,7 @@ __device__ __noinline__ void t1_warp_run(int N, int S, int M, unsigned long long
                                             unsigned long long it_end,
                                             const int8_t *s_A, int8_t *s_B, int *s_d,
                                             int *s_p, unsigned long long *c64,
-                                            WarpPos *pos) {
+                                            WarpPos *pos, ChainStatus *st) {
   const unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31;
   const int NC = S >> 4;
@@ -375,7 +375,7 @@ __device__ __noinline__ void t1_warp_run(int N, int S, int M, unsigned long long
       int dec = 0;
       if (lane == 0) {
         ++n_exact;
-        dec = exact_accept(seed, stream, T0, P, dlt, it + (unsigned)j, &c64[kC64Near]);
+        dec = exact_accept(seed, stream, T0, P, dlt, it + (unsigned)j, &c64[kC64Near], st);
       }
       dec = __shfl_sync(FULL, dec, 0);
       if (!dec) {
@@ -741,7 +741,7 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
       }
       if (warp == 0)
         t1_warp_run<WLPP>(N, S, M, g.seed, g.stream, g.T0, g.P, g.T0f, g.log2a_f, g.mrel,
-                          it_end, s_A, s_B, s_d, s_p, c64, pos);
+                          it_end, s_A, s_B, s_d, s_p, c64, pos, g.st);
       __syncthreads();
       it = ((unsigned long long)pos->it_hi << 32) | pos->it_lo;
       mb = pos->mb;
@@ -994,7 +994,7 @@ __device__ __forceinline__ void t1_run_chain(const ChainDev &g,
         ++c64[kC64Exact];
         s_ctl[kT1Dec] =
             (unsigned)exact_accept(g.seed, g.stream, g.T0, g.P, dlt,
-                                   it + (unsigned)j, &c64[kC64Near]);
+                                   it + (unsigned)j, &c64[kC64Near], g.st);
       }
       __syncthreads();
       if (!s_ctl[kT1Dec]) {

@@ -577,7 +577,8 @@ __device__ __forceinline__ void t2_run_chain(const ChainDev &g,
     const int r = sl.y, s = sl.z, dlt = sl.w;
     if (code & 1u) {  // every CTA decides the same binary64 test
       unsigned long long nt = 0;
-      const int dec = exact_accept(g.seed, g.stream, g.T0, g.P, dlt, it + (unsigned)j, &nt);
+      const int dec = exact_accept(g.seed, g.stream, g.T0, g.P, dlt, it + (unsigned)j, &nt,
+                                   (tid == 0 && rank == 0) ? g.st : nullptr);
       if (tid == 0 && rank == 0) {
         ++c64[kC64Exact];
         c64[kC64Near] += nt;

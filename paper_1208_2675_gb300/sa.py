@@ -43,7 +43,19 @@ class qap_sa_info(ctypes.Structure):
                 ("T0", ctypes.c_double), ("Tf", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("total_iters", ctypes.c_uint64),
                 ("smem_bytes", ctypes.c_uint64), ("direct_iters", ctypes.c_uint64),
-                ("direct_accepts", ctypes.c_uint64), ("warp_iters", ctypes.c_uint64)]
+                ("direct_accepts", ctypes.c_uint64), ("warp_iters", ctypes.c_uint64),
+                ("ctas", ctypes.c_int32), ("threads", ctypes.c_int32)]
+
+
+class qap_peaks(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int32), ("smem_optin_bytes", ctypes.c_int32),
+                ("l2_bytes", ctypes.c_int64), ("sm_mhz", ctypes.c_double),
+                ("smem_bytes_per_clk_sm", ctypes.c_double), ("smem_gbs_chip", ctypes.c_double),
+                ("l2_gbs", ctypes.c_double), ("int32_ops_per_clk_sm", ctypes.c_double),
+                ("dp4a_per_clk_sm", ctypes.c_double), ("cta_barrier_ns", ctypes.c_double),
+                ("cluster_barrier_ns", ctypes.c_double * 5), ("grid_barrier_ns", ctypes.c_double),
+                ("l2_latency_ns", ctypes.c_double), ("dsmem_latency_ns", ctypes.c_double),
+                ("smem_latency_ns", ctypes.c_double)]
 
 
 class qap_problem(ctypes.Structure):
@@ -84,6 +96,9 @@ SIGNATURES = {
     "qap_sa_delta": (ctypes.c_int, [ctypes.c_void_p, _i32p]),
     "qap_sa_temperature": (ctypes.c_double, [ctypes.c_void_p, ctypes.c_uint64]),
     "qap_sa_destroy": (None, [ctypes.c_void_p]),
+    "qap_sa_near_tie_log": (ctypes.c_int, [ctypes.c_void_p, _u64p, ctypes.c_int32, _u64p]),
+    "qap_sa_accept_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _u64p, _u64p,
+                                           _i32p, _i32p]),
     "qap_batch_create": (ctypes.c_int, [ctypes.POINTER(qap_problem), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "qap_batch_run": (ctypes.c_int, [ctypes.c_void_p, _u64p]),
@@ -102,6 +117,7 @@ SIGNATURES = {
     "qap_sa_setup_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p]),
+    "qap_peaks_measure": (ctypes.c_int, [ctypes.POINTER(qap_peaks)]),
     "qap_sa_max_n": (ctypes.c_int32, []),
     "qap_sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -212,6 +228,27 @@ def qap_sa_temperature(h, it: int) -> float:
     return float(lib().qap_sa_temperature(h, int(it)))
 
 
+def qap_sa_near_tie_log(h, cap: int = 8):
+    """(iteration indices of the first near-ties, total near-tie count)."""
+    out = np.zeros(max(cap, 1), dtype=np.uint64)
+    n = ctypes.c_uint64()
+    _check(lib().qap_sa_near_tie_log(h, out.ctypes.data_as(_u64p), int(cap), ctypes.byref(n)),
+           "qap_sa_near_tie_log")
+    return out[:min(cap, 8, n.value)], n.value
+
+
+def qap_sa_accept_probe(h, it, it0, delta) -> np.ndarray:
+    """Eq. (2) decided as the kernels decide it, for probes (it, it0, delta)."""
+    it = np.ascontiguousarray(it, dtype=np.uint64)
+    it0 = np.ascontiguousarray(it0, dtype=np.uint64)
+    dl = np.ascontiguousarray(delta, dtype=np.int32)
+    out = np.zeros(len(it), dtype=np.int32)
+    _check(lib().qap_sa_accept_probe(h, len(it), it.ctypes.data_as(_u64p),
+                                     it0.ctypes.data_as(_u64p), dl.ctypes.data_as(_i32p),
+                                     out.ctypes.data_as(_i32p)), "qap_sa_accept_probe")
+    return out
+
+
 def qap_sa_destroy(h) -> None:
     if h:
         lib().qap_sa_destroy(h)
@@ -224,6 +261,15 @@ def qap_sa_setup_noalloc(A_ptr: int, B_ptr: int, N: int, p_ptr: int, delta_ptr: 
                                       ctypes.c_void_p(p_ptr), ctypes.c_void_p(delta_ptr),
                                       ctypes.c_void_p(cost_ptr), ctypes.c_void_p(stream or None)),
            "qap_sa_setup_noalloc")
+
+
+def qap_peaks_measure() -> dict:
+    """Microbenchmarks of the current device (include/qap_peaks.h)."""
+    pk = qap_peaks()
+    _check(lib().qap_peaks_measure(ctypes.byref(pk)), "qap_peaks_measure")
+    out = {name: getattr(pk, name) for name, _ in qap_peaks._fields_}
+    out["cluster_barrier_ns"] = dict(zip((2, 4, 8, 13, 16), list(pk.cluster_barrier_ns)))
+    return out
 
 
 def qap_sa_max_n() -> int:
@@ -381,6 +427,9 @@ class Chain:
 
     def temperature(self, it: int) -> float:
         return qap_sa_temperature(self.h, it)
+
+    def near_tie_log(self):
+        return qap_sa_near_tie_log(self.h)
 
     def close(self) -> None:
         if getattr(self, "h", None):

@@ -40,11 +40,27 @@ def test_workloads_name_the_measured_configurations(monkeypatch):
     sys.path.insert(0, ROOT)
     import bench
     w = bench.WORKLOADS
+    assert w["c3"]["N"] == 1024 and w["c3"]["I"] == 2 * 10 ** 9 and w["c3"]["side"] == 32
     assert w["n100"]["N"] == 100 and w["n100"]["I"] == 10 ** 8
     assert w["n256"]["N"] == 256 and w["n256"]["I"] == 10 ** 9
     assert w["batch512"]["count"] == 512
     assert (w["batch512"]["n_lo"], w["batch512"]["n_hi"]) == (20, 300)
     assert (w["serve"]["n_lo"], w["serve"]["n_hi"]) == (30, 600)
+    assert w["serve"]["rates"] == (100, 200, 500, 1000, 2000, 5000)
     monkeypatch.setattr(sys, "argv", ["bench.py"])
-    args = bench.parse()  # no flags: one GPU, the N = 100 chain, >= 3 warm-up steps
-    assert args.gpus == 1 and args.workload == "n100" and args.warmup >= 3
+    args = bench.parse()  # no flags: one GPU, the N = 1024 chain, >= 3 warm-up steps
+    assert args.gpus == 1 and args.workload == "c3" and args.warmup >= 3
+
+
+def test_steps_cover_the_whole_schedule():
+    sys.path.insert(0, ROOT)
+    import bench
+    for K in (1, 3, 7, 20, 1000):
+        p = bench.pieces(2 * 10 ** 9, K)
+        assert len(p) == K and sum(p) == 2 * 10 ** 9 and min(p) > 0
+
+
+def test_reference_arm_config_equals_ours(reference_line):
+    sys.path.insert(0, ROOT)
+    import bench
+    assert reference_line["config"] == bench.config_of(bench.WORKLOADS["c3"])

@@ -7,6 +7,8 @@ import oracle
 from paper_1208_2675_gb300 import instances
 from paper_1208_2675_gb300 import sa
 
+from oracle_pool import run_many
+
 pytestmark = pytest.mark.gpu
 
 
@@ -91,3 +93,43 @@ def test_batch_run_in_pieces_and_range_check():
             assert acc == st["accepts"] and cost == st["cost"] and np.array_equal(p, st["p"])
     finally:
         sa.qap_batch_destroy(b)
+
+
+def test_batch512_workload_against_oracle_and_alone():
+    """The 512-chain workload itself -- N ~ U{20..300}, seed 1000 + c, Philox
+    stream c, I = 1e7 each -- in one persistent graph launch, with every SM busy
+    and chains finishing out of order.  Every chain equals the same chain run
+    alone by the single-chain kernel (all 512 run side by side on their own
+    streams), and 32 chains spread over the N range equal the oracle's whole
+    run."""
+    sizes = instances.batch_sizes(512, 20, 300, 4)
+    I = 10 ** 7
+    probs = _problems(sizes, I, 1000)
+    b = sa.qap_batch_create(probs)
+    try:
+        sa.qap_batch_run(b)
+        got = [sa.qap_batch_result(b, c, len(pr["p0"])) for c, pr in enumerate(probs)]
+        tiers = {sa.qap_batch_get_info(b, c)["tier"] for c in range(len(probs))}
+    finally:
+        sa.qap_batch_destroy(b)
+    assert tiers == {1, 2}
+    alone = [sa.Chain(pr["A"], pr["B"], pr["p0"], t0=0.5, tf=1e-3, total_iters=I,
+                      seed=pr["seed"], stream_id=pr["stream_id"]) for pr in probs]
+    for h in alone:
+        h.run_async(I)
+    for c, h in enumerate(alone):
+        h.sync()
+        p1, cost1, acc1 = h.result()
+        p, cost, acc = got[c]
+        assert acc == acc1 and cost == cost1 and np.array_equal(p, p1), c
+        h.close()
+    by_n = np.argsort(sizes, kind="stable")
+    pick = [int(by_n[k]) for k in np.linspace(0, len(sizes) - 1, 32).round().astype(int)]
+    jobs = [(probs[c]["A"], probs[c]["B"], probs[c]["p0"],
+             dict(t0=0.5, tf=1e-3, total_iters=I, seed=probs[c]["seed"],
+                  stream=probs[c]["stream_id"]), I) for c in pick]
+    for c, st in zip(pick, run_many(jobs)):
+        p, cost, acc = got[c]
+        assert acc == st["accepts"] and cost == st["cost"], (c, len(probs[c]["p0"]))
+        assert np.array_equal(p, st["p"])
+        assert st["near_ties"] == 0

@@ -41,8 +41,11 @@ def run_both(A, B, p0, *, t0, tf, I, relative=True, seed=0, stream=0, splits=Non
     p, cost, acc = g.result()
     info = g.info()
     gs = {"p": p, "cost": cost, "accepts": acc, "it": info["iterations"],
-          "near_ties": info["near_ties"], "info": info}
-    out = (gs, o.state(), g.delta(), packed_upper(o.delta()), g, o)
+          "near_ties": info["near_ties"], "info": info,
+          "near_log": [int(x) for x in g.near_tie_log()[0]]}
+    os_ = o.state()
+    os_["near_log"] = [int(x) for x in o.near_tie_log()[0]]
+    out = (gs, os_, g.delta(), packed_upper(o.delta()), g, o)
     return out
 
 
@@ -52,6 +55,9 @@ def assert_same(gs, os_, gd, od):
     assert gs["cost"] == os_["cost"]
     assert np.array_equal(gs["p"], os_["p"])
     assert np.array_equal(gd.astype(np.int64), od)
+    # a flip of an Eq. (2) decision between CUDA's and libm's log could only
+    # occur at a near-tie; both sides log the iterations of theirs
+    assert gs["near_log"] == os_["near_log"]
     assert gs["near_ties"] == 0 and os_["near_ties"] == 0
 
 
@@ -367,3 +373,49 @@ def test_warp_mode_default_threshold_runs_and_matches():
                                      oracle_iters=300000)
     assert_same(gs, os_, gd, od)
     assert gs["info"]["warp_iters"] > 100000
+
+
+def test_n1024_grid_delta_mode_matches_oracle(monkeypatch):
+    """N = 1024 grid instance on its 13-CTA cluster with Delta maintained from
+    the first iteration (Delta tiles in the cluster's Tensor Memory, rows
+    posted over distributed shared memory): 8000 iterations of a schedule
+    over I = 2e9 from T0 = 0.05 mean|Delta0| (about 950 accepted swaps), in
+    three launches, the final Delta element by element."""
+    monkeypatch.setenv("QAPSA_CLUSTER_HYBRID_RATE", "0")
+    A, B, p0 = instances.grid_instance(32, 1)
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.05, tf=1e-3, I=2 * 10 ** 9, seed=1,
+                                     oracle_iters=8000, splits=[1, 3999, 4000])
+    info = g.info()
+    assert info["tier"] == 2 and info["direct_iters"] == 0
+    assert os_["accepts"] > 500
+    assert_same(gs, os_, gd, od)
+
+
+def test_largest_cluster_delta_mode_matches_oracle(monkeypatch):
+    """The largest size the cluster tier takes (16 CTAs) in Delta mode, against
+    the oracle after 10000 iterations, Delta element by element."""
+    monkeypatch.setenv("QAPSA_CLUSTER_HYBRID_RATE", "0")
+    N = sa.qap_sa_max_n()
+    assert N >= 1100
+    A, B, p0 = instances.taixxa_like(N, 61)
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.05, tf=1e-3, I=10 ** 9, seed=61,
+                                     stream=5, oracle_iters=10000, splits=[4000, 6000])
+    assert g.info()["tier"] == 2
+    assert os_["accepts"] > 500
+    assert_same(gs, os_, gd, od)
+
+
+def test_n1024_grid_direct_then_delta_mode_matches_oracle(monkeypatch):
+    """N = 1024 grid instance, a whole schedule of I = 40000 that crosses the
+    cluster tier's mode switch: direct mode through the first block of 16384
+    iterations (acceptance about 0.1), then below the threshold of 0.05 a stop,
+    the Delta rebuild and Delta mode to the end; state and Delta against the
+    oracle."""
+    monkeypatch.setenv("QAPSA_CLUSTER_HYBRID_RATE", "0.05")
+    A, B, p0 = instances.grid_instance(32, 2)
+    I = 40000
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.05, tf=1e-4, I=I, seed=2,
+                                     splits=[20000, 20000])
+    info = g.info()
+    assert info["tier"] == 2 and 16384 <= info["direct_iters"] < I
+    assert_same(gs, os_, gd, od)

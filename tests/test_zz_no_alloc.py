@@ -63,3 +63,28 @@ def test_noalloc_setup_rejects_sizes_beyond_its_maximum():
         sa.qap_sa_setup_noalloc(At.data_ptr(), Bt.data_ptr(), N, pt.data_ptr(),
                                 d_out.data_ptr(), c_out.data_ptr())
     assert e.value.status == sa.QAP_E_RANGE
+
+
+def test_noalloc_setup_rejects_invalid_inputs():
+    """An asymmetric flow matrix and a p that is not a permutation are refused
+    with QAP_E_INVAL, as qap_sa_create refuses them; a valid call afterwards
+    still matches the regular set-up (the array's leftovers are cleared)."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    N = 40
+    A, B, p0 = instances.taixxa_like(N, 5)
+    bad_A = A.copy()
+    bad_A[2, 7] += 1
+    bad_p = p0.copy()
+    bad_p[0] = bad_p[1]
+    d_out = torch.zeros(N * (N - 1) // 2, dtype=torch.int32, device=dev)
+    c_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    for a, p in [(bad_A, p0), (A, bad_p)]:
+        At, Bt, pt = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (a, B, p))
+        with pytest.raises(sa.QapError) as e:
+            sa.qap_sa_setup_noalloc(At.data_ptr(), Bt.data_ptr(), N, pt.data_ptr(),
+                                    d_out.data_ptr(), c_out.data_ptr())
+        assert e.value.status == sa.QAP_E_INVAL
+    want_d, want_c = _regular(A, B, p0)
+    got_d, got_c = _noalloc(torch, A, B, p0, torch.cuda.Stream())
+    assert got_c == want_c and np.array_equal(got_d, want_d)
