@@ -86,6 +86,15 @@ def lib() -> ctypes.CDLL:
         L.orc_chain_get_near_log.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_uint64]
         L.orc_chain_accepts.restype = ctypes.c_int32
         L.orc_chain_accepts.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64]
+        L.orc_delta_entry_general.restype = ctypes.c_int64
+        L.orc_delta_entry_general.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p,
+                                              ctypes.c_int32, ctypes.c_int32]
+        L.orc_chain_set_order.restype = None
+        L.orc_chain_set_order.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        L.orc_chain_is_general.restype = ctypes.c_int32
+        L.orc_chain_is_general.argtypes = [ctypes.c_void_p]
+        L.orc_chain_proposal.restype = None
+        L.orc_chain_proposal.argtypes = [ctypes.c_void_p, ctypes.c_uint64, _i32p, _i32p]
         L.orc_chain_schedule.restype = None
         L.orc_chain_schedule.argtypes = [ctypes.c_void_p, _f64p, _f64p, _f64p]
         L.orc_chain_temperature.restype = ctypes.c_double
@@ -131,6 +140,13 @@ def delta_entry(A, B, p, r: int, s: int) -> int:
                                      _ptr(p, _i32p), r, s))
 
 
+def delta_entry_general(A, B, p, r: int, s: int) -> int:
+    """The swap cost change for any A, B (asymmetric, nonzero diagonals)."""
+    A, B, p = _i32(A), _i32(B), _i32(p)
+    return int(lib().orc_delta_entry_general(len(p), _ptr(A, _i32p), _ptr(B, _i32p),
+                                             _ptr(p, _i32p), r, s))
+
+
 def delta_matrix(A, B, p) -> np.ndarray:
     """Step (a) of section 2.2: full symmetric Delta (int64, zero diagonal)."""
     A, B, p = _i32(A), _i32(B), _i32(p)
@@ -168,7 +184,7 @@ class Chain:
 
     def __init__(self, A, B, p0, *, t0: float, tf: float, total_iters: int,
                  relative: bool = True, seed: int = 0, stream: int = 0,
-                 check: bool = False, log_cap: int = 0):
+                 check: bool = False, log_cap: int = 0, random_order: bool = False):
         self.A, self.B = _i32(A), _i32(B)
         p0 = _i32(p0)
         self.N = len(p0)
@@ -185,6 +201,8 @@ class Chain:
             lib().orc_chain_set_log(self._h, int(log_cap))
         self._log_cap = int(log_cap)
         lib().orc_chain_set_near_log(self._h, 8)
+        if random_order:
+            lib().orc_chain_set_order(self._h, 1)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -222,6 +240,16 @@ class Chain:
 
     def check_failures(self) -> int:
         return int(lib().orc_chain_check_failures(self._h))
+
+    def is_general(self) -> bool:
+        """True when the general (asymmetric) swap-cost forms are in use."""
+        return bool(lib().orc_chain_is_general(self._h))
+
+    def proposal(self, it: int) -> tuple[int, int]:
+        """The pair (r, s), r < s, proposed at iteration it."""
+        r, s = ctypes.c_int32(), ctypes.c_int32()
+        lib().orc_chain_proposal(self._h, int(it), ctypes.byref(r), ctypes.byref(s))
+        return r.value, s.value
 
     def accepts(self, delta: int, it: int) -> bool:
         """Eq. (2) (reading R3) for swap cost delta proposed at iteration it."""

@@ -23,6 +23,9 @@
  *   orc_delta_entry         closed form of the same change for symmetric,
  *                           zero-diagonal A and B (derived from Eq. (1); the
  *                           paper cites Taillard for it and prints no formula).
+ *   orc_delta_entry_general the same change for any A and B (asymmetric,
+ *                           nonzero diagonals): the general swap cost, derived
+ *                           from Eq. (1) the same way.
  *   orc_philox4x32_10       Philox4x32-10 of Salmon et al., SC'11 ("Parallel
  *                           random numbers: as easy as 1, 2, 3").
  *   orc_uniform             the uniform r of Eq. (2), section 2.1.
@@ -48,6 +51,13 @@
  *   R5 relative temperatures: T0 = t0 * (sum_{r<s} |Delta0_rs|) / M,
  *      Tf = tf * T0; an instance with Delta0 == 0 everywhere uses t0, tf as
  *      absolute temperatures.
+ *   R6 random proposal order (section 2.1, "determined randomly"), chosen with
+ *      orc_chain_set_order: the pair proposed at iteration it is pair number
+ *      m = (x * M) >> 32 of the row-major enumeration, x word 0 of
+ *      Philox4x32-10(counter = (it low, it high, stream, 1), key = seed).
+ *   R7 general instances: when A or B is not symmetric with a zero diagonal,
+ *      the swap costs and their update use the general forms
+ *      (orc_delta_entry_general, orc_apply_swap), else the symmetric ones.
  */
 #include <math.h>
 #include <stdint.h>
@@ -101,6 +111,44 @@ EXPORT int64_t orc_delta_entry(int32_t N, const int32_t *A, const int32_t *B,
     acc += a * b;
   }
   return 2 * acc;
+}
+
+/* The same change for any A and B.  Write B'[x][y] = B[p(x)][p(y)].  The
+ * terms of Eq. (1) with neither index in {r, s} do not change; those with one
+ * index in {r, s} give, for every other k, the row and the column sums below;
+ * the four terms with both indices in {r, s} give the first two products:
+ *   Delta_rs = (A[r][r] - A[s][s]) (B'[s][s] - B'[r][r])
+ *            + (A[r][s] - A[s][r]) (B'[s][r] - B'[r][s])
+ *            + sum_{k not in {r,s}} (A[r][k] - A[s][k]) (B'[s][k] - B'[r][k])
+ *                                 + (A[k][r] - A[k][s]) (B'[k][s] - B'[k][r]). */
+EXPORT int64_t orc_delta_entry_general(int32_t N, const int32_t *A,
+                                       const int32_t *B, const int32_t *p,
+                                       int32_t r, int32_t s) {
+#define ORC_A(i, j) ((int64_t)A[(int64_t)(i) * N + (j)])
+#define ORC_BP(i, j) ((int64_t)B[(int64_t)p[i] * N + p[j]])
+  int64_t d = (ORC_A(r, r) - ORC_A(s, s)) * (ORC_BP(s, s) - ORC_BP(r, r)) +
+              (ORC_A(r, s) - ORC_A(s, r)) * (ORC_BP(s, r) - ORC_BP(r, s));
+  for (int32_t k = 0; k < N; ++k) {
+    if (k == r || k == s) continue;
+    d += (ORC_A(r, k) - ORC_A(s, k)) * (ORC_BP(s, k) - ORC_BP(r, k)) +
+         (ORC_A(k, r) - ORC_A(k, s)) * (ORC_BP(k, s) - ORC_BP(k, r));
+  }
+#undef ORC_A
+#undef ORC_BP
+  return d;
+}
+
+/* 1 if A and B are both symmetric with a zero diagonal (the instance family of
+ * section 4), for which orc_delta_entry holds. */
+static int orc_is_symmetric_family(int32_t N, const int32_t *A, const int32_t *B) {
+  for (int32_t i = 0; i < N; ++i) {
+    if (A[(int64_t)i * N + i] != 0 || B[(int64_t)i * N + i] != 0) return 0;
+    for (int32_t j = i + 1; j < N; ++j)
+      if (A[(int64_t)i * N + j] != A[(int64_t)j * N + i] ||
+          B[(int64_t)i * N + j] != B[(int64_t)j * N + i])
+        return 0;
+  }
+  return 1;
 }
 
 /* Step (a) of section 2.2: the matrix of the costs of every possible swap
@@ -233,6 +281,8 @@ typedef struct {
   uint64_t log_cap, log_n;
   uint64_t *nlog;       /* iteration index of each near-tie (R3) */
   uint64_t nlog_cap;
+  int32_t general;      /* R7: the general swap-cost forms are in use */
+  int32_t random_order; /* R6: proposals drawn at random */
 } orc_chain;
 
 static void orc_pair_of(int32_t N, int64_t m, int32_t *r, int32_t *s) {
@@ -263,7 +313,19 @@ EXPORT orc_chain *orc_chain_create(int32_t N, const int32_t *A,
   memcpy(c->B, B, sizeof(int32_t) * n2);
   memcpy(c->p, p0, sizeof(int32_t) * (size_t)N);
   /* Step (a): initial Delta and the cost of Eq. (1). */
-  orc_delta_matrix(N, c->A, c->B, c->p, c->D);
+  c->general = !orc_is_symmetric_family(N, c->A, c->B);
+  if (c->general) {
+    for (int32_t r = 0; r < N; ++r) {
+      c->D[(int64_t)r * N + r] = 0;
+      for (int32_t s = r + 1; s < N; ++s) {
+        int64_t d = orc_delta_entry_general(N, c->A, c->B, c->p, r, s);
+        c->D[(int64_t)r * N + s] = d;
+        c->D[(int64_t)s * N + r] = d;
+      }
+    }
+  } else {
+    orc_delta_matrix(N, c->A, c->B, c->p, c->D);
+  }
   c->cost = orc_cost(N, c->A, c->B, c->p);
   double T0 = t0, Tf = tf;
   if (relative) { /* R5 */
@@ -298,6 +360,13 @@ EXPORT void orc_chain_destroy(orc_chain *c) {
 }
 
 EXPORT void orc_chain_set_check(orc_chain *c, int32_t on) { c->check = on; }
+
+/* R6: 1 = proposals drawn at random, 0 = sequential cyclic order (default). */
+EXPORT void orc_chain_set_order(orc_chain *c, int32_t random_order) {
+  c->random_order = random_order ? 1 : 0;
+}
+
+EXPORT int32_t orc_chain_is_general(const orc_chain *c) { return c->general; }
 EXPORT int64_t orc_chain_check_failures(const orc_chain *c) {
   return c->check_failures;
 }
@@ -422,6 +491,75 @@ static void orc_apply_swap(orc_chain *c, int32_t r, int32_t s, int64_t delta) {
   c->accepts++;
 }
 
+/* The same step for general A and B (R7).  A cell (u,v) disjoint from {r,s}
+ * sees different B entries only in the k = r and k = s terms of its row sum
+ * and of its column sum (orc_delta_entry_general), which gives, with p the
+ * assignment BEFORE the swap and B'[x][y] = B[p(x)][p(y)],
+ *   Delta_uv += (A[r][u] - A[r][v] - A[s][u] + A[s][v])
+ *               (B'[s][v] - B'[s][u] - B'[r][v] + B'[r][u])
+ *             + (A[u][r] - A[v][r] - A[u][s] + A[v][s])
+ *               (B'[v][s] - B'[u][s] - B'[v][r] + B'[u][r]);
+ * with A, B symmetric the two products are equal (the symmetric form).  Cells
+ * in rows or columns r, s are recomputed from the definition after the swap. */
+static void orc_apply_swap_general(orc_chain *c, int32_t r, int32_t s, int64_t delta) {
+  const int32_t N = c->N;
+  const int32_t *A = c->A, *B = c->B;
+  int32_t *p = c->p;
+  int64_t *D = c->D;
+#define ORC_A(i, j) ((int64_t)A[(int64_t)(i) * N + (j)])
+#define ORC_BP(i, j) ((int64_t)B[(int64_t)p[i] * N + p[j]])
+  for (int32_t u = 0; u < N; ++u) {
+    if (u == r || u == s) continue;
+    for (int32_t v = u + 1; v < N; ++v) {
+      if (v == r || v == s) continue;
+      int64_t a1 = ORC_A(r, u) - ORC_A(r, v) - ORC_A(s, u) + ORC_A(s, v);
+      int64_t b1 = ORC_BP(s, v) - ORC_BP(s, u) - ORC_BP(r, v) + ORC_BP(r, u);
+      int64_t a2 = ORC_A(u, r) - ORC_A(v, r) - ORC_A(u, s) + ORC_A(v, s);
+      int64_t b2 = ORC_BP(v, s) - ORC_BP(u, s) - ORC_BP(v, r) + ORC_BP(u, r);
+      D[(int64_t)u * N + v] += a1 * b1 + a2 * b2;
+      D[(int64_t)v * N + u] = D[(int64_t)u * N + v];
+    }
+  }
+#undef ORC_A
+#undef ORC_BP
+  const int32_t t = p[r];
+  p[r] = p[s];
+  p[s] = t;
+  c->cost += delta;
+  for (int32_t v = 0; v < N; ++v) {
+    if (v != r) {
+      int64_t d = orc_delta_entry_general(N, A, B, p, r, v);
+      D[(int64_t)r * N + v] = d;
+      D[(int64_t)v * N + r] = d;
+    }
+    if (v != s) {
+      int64_t d = orc_delta_entry_general(N, A, B, p, s, v);
+      D[(int64_t)s * N + v] = d;
+      D[(int64_t)v * N + s] = d;
+    }
+  }
+  c->accepts++;
+}
+
+/* R6: the pair proposed at iteration it under random order. */
+static void orc_random_pair(const orc_chain *c, uint64_t it, int32_t *r, int32_t *s) {
+  uint32_t ctr[4] = {(uint32_t)it, (uint32_t)(it >> 32), c->stream, 1u};
+  uint32_t key[2] = {(uint32_t)c->seed, (uint32_t)(c->seed >> 32)};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  int64_t m = (int64_t)(((uint64_t)out[0] * (uint64_t)c->M) >> 32);
+  orc_pair_of(c->N, m, r, s);
+}
+
+/* The pair the chain proposes at iteration it (R1 or R6); for sequential order
+ * this is pair number it mod M. */
+EXPORT void orc_chain_proposal(const orc_chain *c, uint64_t it, int32_t *r, int32_t *s) {
+  if (c->random_order)
+    orc_random_pair(c, it, r, s);
+  else
+    orc_pair_of(c->N, (int64_t)(it % (uint64_t)c->M), r, s);
+}
+
 static void orc_check_state(orc_chain *c) {
   const int32_t N = c->N;
   if (orc_cost(N, c->A, c->B, c->p) != c->cost) c->check_failures++;
@@ -455,6 +593,7 @@ EXPORT int32_t orc_chain_run(orc_chain *c, uint64_t iters,
   for (; c->it < end; c->it++) {
     int32_t r = c->cur_r, s = c->cur_s;
     orc_advance_cursor(c);
+    if (c->random_order) orc_random_pair(c, c->it, &r, &s);
     int64_t delta = traditional
                         ? orc_swap_cost_change(N, c->A, c->B, c->p, r, s)
                         : c->D[(int64_t)r * N + s];
@@ -468,7 +607,10 @@ EXPORT int32_t orc_chain_run(orc_chain *c, uint64_t iters,
       c->cost += delta;
       c->accepts++;
     } else {
-      orc_apply_swap(c, r, s, delta);
+      if (c->general)
+        orc_apply_swap_general(c, r, s, delta);
+      else
+        orc_apply_swap(c, r, s, delta);
       if (c->check) orc_check_state(c);
     }
   }

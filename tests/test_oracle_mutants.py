@@ -52,6 +52,33 @@ MUTANTS = {
     "philox_multiplier": ("const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;",
                           "const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D55u;"),
     "philox_key_word": ("uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi1 ^ c1 ^ k1;"),
+    # the general (asymmetric) swap cost and its update
+    "general_entry_diag_sign": ("(ORC_A(r, r) - ORC_A(s, s)) * (ORC_BP(s, s) - ORC_BP(r, r))",
+                                "(ORC_A(r, r) - ORC_A(s, s)) * (ORC_BP(r, r) - ORC_BP(s, s))"),
+    "general_entry_pair_transposed": ("(ORC_A(r, s) - ORC_A(s, r)) * (ORC_BP(s, r) - ORC_BP(r, s))",
+                                      "(ORC_A(r, s) - ORC_A(s, r)) * (ORC_BP(r, s) - ORC_BP(s, r))"),
+    "general_entry_dropped_column_sum": (
+        "    d += (ORC_A(r, k) - ORC_A(s, k)) * (ORC_BP(s, k) - ORC_BP(r, k)) +\n"
+        "         (ORC_A(k, r) - ORC_A(k, s)) * (ORC_BP(k, s) - ORC_BP(k, r));",
+        "    d += 2 * (ORC_A(r, k) - ORC_A(s, k)) * (ORC_BP(s, k) - ORC_BP(r, k));"),
+    "general_update_symmetric_shortcut": ("      D[(int64_t)u * N + v] += a1 * b1 + a2 * b2;",
+                                          "      D[(int64_t)u * N + v] += 2 * a1 * b1;"),
+    "general_update_transposed": (
+        "      int64_t a2 = ORC_A(u, r) - ORC_A(v, r) - ORC_A(u, s) + ORC_A(v, s);",
+        "      int64_t a2 = ORC_A(r, u) - ORC_A(r, v) - ORC_A(s, u) + ORC_A(s, v);"),
+    "general_recompute_symmetric_form": (
+        "      int64_t d = orc_delta_entry_general(N, A, B, p, r, v);",
+        "      int64_t d = orc_delta_entry(N, A, B, p, r, v);"),
+    "family_check_ignores_diagonal": (
+        "    if (A[(int64_t)i * N + i] != 0 || B[(int64_t)i * N + i] != 0) return 0;", ""),
+    # random proposal order
+    "random_pair_word": ("int64_t m = (int64_t)(((uint64_t)out[0] * (uint64_t)c->M) >> 32);",
+                         "int64_t m = (int64_t)(((uint64_t)out[1] * (uint64_t)c->M) >> 32);"),
+    "random_pair_counter_word": (
+        "  uint32_t ctr[4] = {(uint32_t)it, (uint32_t)(it >> 32), c->stream, 1u};",
+        "  uint32_t ctr[4] = {(uint32_t)it, (uint32_t)(it >> 32), c->stream, 0u};"),
+    "random_pair_scale": ("int64_t m = (int64_t)(((uint64_t)out[0] * (uint64_t)c->M) >> 32);",
+                          "int64_t m = (int64_t)(((uint64_t)out[0] * (uint64_t)(c->M - 1)) >> 32);"),
 }
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -88,6 +115,7 @@ def _build(src_text: str, tmpdir: str, name: str) -> ctypes.CDLL:
     L.orc_chain_get_log.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_uint64]
     L.orc_chain_schedule.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.orc_chain_set_order.argtypes = [ctypes.c_void_p, ctypes.c_int32]
     return L
 
 
@@ -131,11 +159,47 @@ def _pins_hold(L) -> bool:
             return False
     # (5) a chain: replay every decision against Eq. (2) in exponential form with
     #     brute-force deltas, u from the published counter layout, T against
-    #     T0 alpha^it; the final Delta against brute force
-    N, I, seed = 8, 3000, 11
-    A, B, p0 = instances.taixxa_like(N, 5)
+    #     T0 alpha^it; the final Delta against brute force.  Then the same for
+    #     general instances (asymmetric; symmetric with a nonzero diagonal) and
+    #     for random proposal order, with the pair drawn by its definition.
+    A, B, p0 = instances.taixxa_like(8, 5)
+    if not _chain_replay_holds(L, A, B, p0, 3000, 11, check_schedule=True):
+        return False
+    rng = np.random.default_rng(9)
+    Ag = rng.integers(-20, 40, size=(7, 7)).astype(np.int32)
+    Bg = rng.integers(-20, 40, size=(7, 7)).astype(np.int32)
+    if not _chain_replay_holds(L, Ag, Bg, rng.permutation(7).astype(np.int32), 2000, 12):
+        return False
+    As, Bs, ps = instances.taixxa_like(7, 6)
+    As, Bs = As.copy(), Bs.copy()
+    np.fill_diagonal(As, rng.integers(1, 30, size=7))
+    np.fill_diagonal(Bs, rng.integers(1, 30, size=7))
+    if not _chain_replay_holds(L, As, Bs, ps, 2000, 13):
+        return False
+    A, B, p0 = instances.taixxa_like(8, 7)
+    if not _chain_replay_holds(L, A, B, p0, 2000, 14, random_order=True):
+        return False
+    return True
+
+
+def _random_pair(seed, stream, it, M, pairs):
+    """The reading of random order: pair number (x M) >> 32, x word 0 of Philox
+    at counter (it, stream, 1) -- through the published (pinned) Philox."""
+    import oracle as ref
+    x = int(ref.philox4x32_10([it & 0xFFFFFFFF, it >> 32, stream, 1],
+                              [seed & 0xFFFFFFFF, seed >> 32])[0])
+    return pairs[(x * M) >> 32]
+
+
+def _chain_replay_holds(L, A, B, p0, I, seed, check_schedule=False, random_order=False):
+    import oracle as ref
+    ptr = lambda a, t: a.ctypes.data_as(t)
+    N = len(p0)
+    A, B, p0 = (np.ascontiguousarray(x, dtype=np.int32) for x in (A, B, p0))
     h = L.orc_chain_create(N, ptr(A, _i32p), ptr(B, _i32p), ptr(p0, _i32p), 0.5, 1e-2, I, 1,
                            seed, 0)
+    if random_order:
+        L.orc_chain_set_order(h, 1)
     L.orc_chain_set_log(h, I)
     L.orc_chain_run(h, I, 0)
     log = np.zeros(I, dtype=np.uint64)
@@ -144,17 +208,20 @@ def _pins_hold(L) -> bool:
     T0, Tf, al = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     L.orc_chain_schedule(h, ctypes.byref(T0), ctypes.byref(Tf), ctypes.byref(al))
     pairs = [(r, s) for r in range(N) for s in range(r + 1, N)]
-    # the schedule's parameters from their definitions: T0 = 0.5 mean |Delta_0|
-    # over the M pairs (brute-force swap costs), Tf = 1e-2 T0, alpha = (Tf/T0)^(1/(I-1))
     c0 = _loc_cost(A, B, p0)
-    sum_abs = sum(abs(_loc_cost(A, B, _swapped(p0, r, s)) - c0) for r, s in pairs)
-    if T0.value != 0.5 * (sum_abs / len(pairs)) or Tf.value != 1e-2 * T0.value:
-        return False
-    if abs(al.value / (Tf.value / T0.value) ** (1.0 / (I - 1)) - 1.0) > 1e-12:
-        return False
+    if check_schedule:
+        # the schedule's parameters from their definitions: T0 = 0.5 mean |Delta_0|
+        # over the M pairs (brute-force swap costs), Tf = 1e-2 T0,
+        # alpha = (Tf/T0)^(1/(I-1))
+        sum_abs = sum(abs(_loc_cost(A, B, _swapped(p0, r, s)) - c0) for r, s in pairs)
+        if T0.value != 0.5 * (sum_abs / len(pairs)) or Tf.value != 1e-2 * T0.value:
+            return False
+        if abs(al.value / (Tf.value / T0.value) ** (1.0 / (I - 1)) - 1.0) > 1e-12:
+            return False
     q = np.array(p0, copy=True)
     for it in range(I):
-        r, s = pairs[it % len(pairs)]
+        r, s = (_random_pair(seed, 0, it, len(pairs), pairs) if random_order
+                else pairs[it % len(pairs)])
         delta = _loc_cost(A, B, _swapped(q, r, s)) - _loc_cost(A, B, q)
         T = L.orc_chain_temperature(h, it)
         if abs(T / (T0.value * al.value ** it) - 1) > 1e-9:
