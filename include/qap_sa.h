@@ -15,8 +15,12 @@
  *   - Matrices are row-major N x N int32 (element (i,j) at index i*N + j).
  *     A[i][j] is the flow between facilities i and j, B[x][y] the distance
  *     between locations x and y; p[i] is the location of facility i.
- *     Version 1 accepts the symmetric case with zero diagonals (the instance
- *     family of section 4) and entries in [-127, 127].
+ *     Any int32 entries are accepted as long as 8 N max|A| max|B| <= 2^31 - 1
+ *     (every swap cost and Gram sum then fits int32).  The symmetric instances
+ *     with zero diagonals and entries in [-127, 127] (the family of section 4)
+ *     run on the on-chip tiers; asymmetric instances (the general swap cost),
+ *     nonzero diagonals, wider entries, random proposal order and N beyond a
+ *     cluster's capacity run on tier 3 (qap_sa_info.tier).
  *   - Unless a name ends in _device, pointers are HOST pointers; the library
  *     copies what it needs and never keeps a caller pointer after returning.
  *   - Return value: QAP_OK (0) or a negative QAP_E_* status; on error nothing
@@ -44,16 +48,17 @@ extern "C" {
 /* ---- status codes ------------------------------------------------------- */
 #define QAP_OK            0
 #define QAP_E_INVAL      (-1) /* null pointer; N < 2; p0 not a permutation;
-                                 A or B not symmetric or diagonal not zero;
-                                 T0 or Tf not finite and > 0; total_iters == 0 */
-#define QAP_E_RANGE      (-2) /* an entry outside [-127, 127]; the swap-cost
-                                 bound 8 N max|A| max|B| exceeds 2^31 - 1;
-                                 or it + iters > total_iters */
+                                 T0 or Tf not finite and > 0; total_iters == 0;
+                                 unknown schedule flags */
+#define QAP_E_RANGE      (-2) /* the swap-cost bound 8 N max|A| max|B| exceeds
+                                 2^31 - 1; or it + iters > total_iters */
 #define QAP_E_NOMEM      (-3) /* device or host allocation failed */
 #define QAP_E_CUDA       (-4) /* a CUDA call failed (message via strerror) */
 #define QAP_E_TIMEOUT    (-5) /* a bounded device-side wait expired */
 #define QAP_E_STATE      (-6) /* the device reported an inconsistent state */
-#define QAP_E_UNSUPPORTED (-7) /* N larger than the largest supported tier (qap_sa_max_n) */
+#define QAP_E_UNSUPPORTED (-7) /* N larger than the largest supported tier
+                                  (qap_sa_max_n, qap_sa_max_n_tier); a tier-3
+                                  chain in a batch or a served request */
 
 /* ---- cooling schedule ---------------------------------------------------- */
 /* Temperature T of Eq. (2) is lowered after every iteration (section 2.1) by
@@ -63,12 +68,18 @@ extern "C" {
 #define QAP_T_RELATIVE 1u /* t0 multiplies mean |Delta_0| over the M pairs,
                              tf multiplies T0; if every Delta_0 is zero t0 and
                              tf are used as absolute temperatures */
+#define QAP_ORDER_RANDOM 2u /* proposals drawn at random (section 2.1) instead
+                             of the sequential cyclic order: the pair proposed
+                             at iteration it is pair number (x * M) >> 32 of
+                             the row-major enumeration, x word 0 of
+                             Philox4x32-10(counter = (it low, it high,
+                             stream_id, 1), key = (seed low, seed high)) */
 
 typedef struct qap_schedule {
   double t0;            /* T0, or its multiplier with QAP_T_RELATIVE        */
   double tf;            /* Tf, or its multiplier with QAP_T_RELATIVE        */
   uint64_t total_iters; /* I: the schedule spans it = 0 .. I - 1 (>= 1)     */
-  uint32_t flags;       /* QAP_T_RELATIVE or 0                              */
+  uint32_t flags;       /* QAP_T_RELATIVE | QAP_ORDER_RANDOM, or 0          */
   uint32_t stream_id;   /* Philox counter word 2: the chain's random stream */
 } qap_schedule;
 
@@ -137,7 +148,11 @@ typedef struct qap_sa_info {
                              Tensor Memory, A and B' in its shared memory);
                              2 = a thread-block cluster (Delta in the
                              cluster's Tensor Memory, A and B' split over the
-                             cluster's shared memory), for N beyond one SM */
+                             cluster's shared memory), for N beyond one SM;
+                             3 = a persistent grid (Delta in global memory,
+                             rows staged by TMA, one grid barrier per
+                             accepted swap) for general instances, random
+                             order, wide entries and N beyond a cluster    */
   uint64_t iterations;    /* it: iterations done                            */
   uint64_t accepts;
   int64_t cost;
@@ -262,7 +277,10 @@ typedef struct qap_server qap_server; /* opaque; freed by qap_server_stop */
 /* Starts the worker on the current device; cfg may be NULL.                  */
 QAP_EXPORT int qap_server_start(const qap_server_cfg *cfg, qap_server **out);
 /* Queues `iters` iterations of problem q (inputs copied during the call;
- * iters <= q->sched.total_iters); *ticket identifies the request.            */
+ * iters <= q->sched.total_iters); *ticket identifies the request.  Only chains
+ * of the on-chip tiers are served (symmetric, zero diagonal, entries in
+ * [-127, 127], sequential order, N <= qap_sa_max_n_tier(2)); others return
+ * QAP_E_UNSUPPORTED.                                                         */
 QAP_EXPORT int qap_server_submit(qap_server *s, const qap_problem *q,
                                  uint64_t iters, uint64_t *ticket);
 /* Non-blocking: fills *out (out->done = 0 while pending); when done and p_out
@@ -302,9 +320,14 @@ QAP_EXPORT int qap_sa_setup_noalloc(const int32_t *A, const int32_t *B, int32_t 
                                     int64_t *cost_out, void *cuda_stream);
 
 /* ---- library ------------------------------------------------------------- */
-/* Largest N any tier supports on the current device (0 if no device): about
- * 276 on one SM, about 1100 on a cluster of up to 16 SMs.                   */
+/* Largest N any tier supports on the current device (0 if no device).      */
 QAP_EXPORT int32_t qap_sa_max_n(void);
+
+/* Largest N of one tier on the current device (0 if no device or an unknown
+ * tier): 1 = one SM (about 276), 2 = a cluster of up to 16 SMs (1136),
+ * 3 = the grid tier for symmetric instances, 4 = the grid tier for general
+ * (asymmetric) instances.                                                    */
+QAP_EXPORT int32_t qap_sa_max_n_tier(int32_t tier);
 
 /* Static text for a status code; for QAP_E_CUDA the last CUDA error text of
  * the calling thread is appended.                                            */

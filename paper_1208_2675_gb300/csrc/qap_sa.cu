@@ -15,10 +15,14 @@
 #include "qap_sa.h"
 #include "qap_internal.h"
 #include "sa_tier2.cuh"
+#include "sa_tier3.cuh"
 
 #include <vector>
 
 using namespace qapsa;
+
+__global__ void classify_kernel(const int *A32, const int *B32, const int *p0, int N,
+                                int *count, SetupOut *out);
 
 namespace {
 
@@ -182,6 +186,14 @@ struct qap_sa {
   int smem_bytes = 0;   // dynamic shared memory of the SA kernel
   unsigned long long it_host = 0;  // iterations enqueued so far
   int tier = 1;
+  // tier 3 (a persistent grid, Delta in global memory)
+  int general = 0;                 // the general (asymmetric) swap-cost forms
+  int random_order = 0;            // proposals drawn at random
+  int *A3 = nullptr, *AT3 = nullptr, *B3 = nullptr, *BT3 = nullptr;
+  int *Ad3 = nullptr, *Bd3 = nullptr, *dR3 = nullptr, *dC3 = nullptr;
+  unsigned long long *bar3 = nullptr;
+  unsigned *keys3 = nullptr;
+  T3Dev dev3{};
 };
 
 namespace {
@@ -206,6 +218,16 @@ void free_handle(qap_sa *h) {
   dfree(h->st, st);
   dfree(h->P, st);
   dfree(h->tiles, st);
+  dfree(h->A3, st);
+  if (h->AT3 != h->A3) dfree(h->AT3, st);
+  dfree(h->B3, st);
+  if (h->BT3 != h->B3) dfree(h->BT3, st);
+  dfree(h->Ad3, st);
+  dfree(h->Bd3, st);
+  dfree(h->dR3, st);
+  dfree(h->dC3, st);
+  dfree(h->bar3, st);
+  dfree(h->keys3, st);
   if (h->own_stream && st) cudaStreamDestroy(st);
   delete h;
 }
@@ -255,6 +277,11 @@ void preload_kernels() {
     cudaFuncGetAttributes(&a, setup_delta_kernel);
     cudaFuncGetAttributes(&a, rebuild_delta_kernel);
     cudaFuncGetAttributes(&a, clear_rebuild_kernel);
+    cudaFuncGetAttributes(&a, classify_kernel);
+    cudaFuncGetAttributes(&a, t3_pack_kernel);
+    cudaFuncGetAttributes(&a, t3_perm_kernel);
+    cudaFuncGetAttributes(&a, t3_gram_kernel);
+    cudaFuncGetAttributes(&a, t3_delta_kernel);
     const int smem = device_smem_optin();
     // the limit covers dynamic shared memory only: the kernel's static part
     // comes off the device's opt-in size
@@ -269,6 +296,8 @@ void preload_kernels() {
     give_all((const void *)sa_batch_kernel);
     give_all((const void *)sa_tier2_kernel);
     give_all((const void *)sa_tier2_batch_kernel);
+    give_all((const void *)sa_tier3_kernel<false>);
+    give_all((const void *)sa_tier3_kernel<true>);
     cudaFuncSetAttribute(sa_tier2_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(sa_tier2_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
                          1);
@@ -351,7 +380,7 @@ int tier2_fits(int N) {
 }
 
 
-int max_n_any() {
+int max_n_tier2() {
   static int cached = -1;
   if (cached >= 0) return cached;
   preload_kernels();
@@ -362,6 +391,48 @@ int max_n_any() {
   }
   cached = best;
   return best;
+}
+
+// Tier 3: the largest N whose shared-memory vectors fit one CTA (symmetric
+// instances need fewer vectors than general ones).
+int max_n_tier3(bool general) {
+  const int optin = device_smem_optin();
+  int N = 2;
+  while (t3_smem_bytes(N + 4, general) + 64 <= optin) N += 4;
+  while (t3_smem_bytes(N + 1, general) + 64 <= optin) ++N;
+  return N;
+}
+
+int max_n_any() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  const int t2 = max_n_tier2(), t3 = max_n_tier3(false);
+  cached = t2 > t3 ? t2 : t3;
+  return cached;
+}
+
+// CTAs of a tier-3 grid: one per SM, fewer for small problems (about 256 cells
+// of Delta each at least), within what a cooperative launch can keep resident.
+int tier3_grid(int N, bool general) {
+  int dev = 0, sms = 1, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void *k = general ? (const void *)sa_tier3_kernel<true> : (const void *)sa_tier3_kernel<false>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kT3Threads,
+                                                    t3_smem_bytes(N, general)) != cudaSuccess) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  const long long M = (long long)N * (N - 1) / 2;
+  long long G = M / 256;
+  if (G < 1) G = 1;
+  if (G > sms) G = sms;
+  if (G > (long long)nb * sms) G = (long long)nb * sms;
+  if (const char *e = getenv("QAPSA_T3_GRID")) {
+    const long long x = atoll(e);
+    if (x >= 1 && x <= (long long)nb * sms) G = x;
+  }
+  return (int)G;
 }
 
 cudaError_t launch_tier2(const ChainDev &g, unsigned long long it_end, int C,
@@ -395,6 +466,208 @@ void keep_pool_memory() {
   done[dev] = true;
 }
 
+}  // namespace
+
+// Classifies an instance for the choice of tier: symmetry, zero diagonals,
+// entries within int8, the largest magnitudes, and whether p0 is a permutation.
+__global__ void classify_kernel(const int *A32, const int *B32, const int *p0, int N,
+                                int *count, SetupOut *out) {
+  int flags = 0, ma = 0, mb = 0;
+  const long long NN = (long long)N * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < NN;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx - (long long)i * N);
+    const int a = A32[idx], b = B32[idx];
+    if (a != A32[(long long)j * N + i] || b != B32[(long long)j * N + i]) flags |= kFlagAsym;
+    if (i == j && (a != 0 || b != 0)) flags |= kFlagDiag;
+    const int aa = a < 0 ? (a == INT_MIN ? INT_MAX : -a) : a;
+    const int ab = b < 0 ? (b == INT_MIN ? INT_MAX : -b) : b;
+    ma = max(ma, aa);
+    mb = max(mb, ab);
+    if (aa > 127) flags |= kFlagRangeA;
+    if (ab > 127) flags |= kFlagRangeB;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int v = p0[i];
+    if (v < 0 || v >= N) flags |= kFlagPerm;
+    else atomicAdd(count + v, 1);
+  }
+  flags = __reduce_or_sync(0xFFFFFFFFu, flags);
+  ma = __reduce_max_sync(0xFFFFFFFFu, ma);
+  mb = __reduce_max_sync(0xFFFFFFFFu, mb);
+  if ((threadIdx.x & 31) == 0) {
+    if (flags) atomicOr(&out->flags, flags);
+    atomicMax(&out->max_abs_a, ma);
+    atomicMax(&out->max_abs_b, mb);
+  }
+}
+
+__global__ void classify_perm_kernel(const int *count, int N, SetupOut *out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    if (count[i] != 1) atomicOr(&out->flags, kFlagPerm);
+}
+
+namespace {
+
+int classify(const int32_t *A32, const int32_t *B32, int32_t N, const int32_t *p032,
+             cudaStream_t stream, SetupOut *res) {
+  int *count = nullptr;
+  SetupOut *so = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&count, sizeof(int) * N, stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&so, sizeof(SetupOut), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(int) * N, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(so, 0, sizeof(SetupOut), stream);
+  if (e == cudaSuccess) {
+    const long long NN = (long long)N * N;
+    const int blocks = (int)((NN + 255) / 256 < 4096 ? (NN + 255) / 256 : 4096);
+    classify_kernel<<<blocks, 256, 0, stream>>>(A32, B32, p032, N, count, so);
+    classify_perm_kernel<<<(N + 255) / 256, 256, 0, stream>>>(count, N, so);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(res, so, sizeof *res, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  dfree(count, stream);
+  dfree(so, stream);
+  return e == cudaSuccess ? QAP_OK : cuda_fail(e, "classify");
+}
+
+// Tier 3 set-up (step (a) of section 2.2): static rows of A, B (and their
+// transposes for general instances), Delta_0 from the Gram sums, the Gram
+// diagonals, C0, the schedule.  h has its stream and sizes; on failure the
+// caller frees h.
+int create_tier3(qap_sa *h, const int32_t *A32, const int32_t *B32, const int32_t *p032,
+                 const qap_schedule *sc, uint64_t seed, bool general, bool random,
+                 const SetupOut &cls) {
+  const int N = h->N, M = h->M;
+  cudaStream_t stream = h->stream;
+  if (N > max_n_tier3(general)) return QAP_E_UNSUPPORTED;
+  // Swap costs and the Gram sums behind them stay below 8 N max|A| max|B|.
+  if (8.0 * N * (double)cls.max_abs_a * (double)cls.max_abs_b > 2147483647.0)
+    return QAP_E_RANGE;
+  h->tier = 3;
+  h->general = general ? 1 : 0;
+  h->random_order = random ? 1 : 0;
+  const int SA = t3_np(N);
+  const size_t rows = (size_t)N * SA * sizeof(int);
+  int *count = nullptr;
+  long long *R = nullptr, *C = nullptr;
+  SetupOut *so = nullptr;
+  auto done = [&](int code) {
+    dfree(count, stream);
+    dfree(R, stream);
+    if (C != R) dfree(C, stream);
+    dfree(so, stream);
+    return code;
+  };
+#define CK3(call)                                            \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return done(cuda_fail(e_, #call)); \
+  } while (0)
+  CK3(cudaMallocAsync((void **)&h->A3, rows, stream));
+  CK3(cudaMallocAsync((void **)&h->B3, rows, stream));
+  if (general) {
+    CK3(cudaMallocAsync((void **)&h->AT3, rows, stream));
+    CK3(cudaMallocAsync((void **)&h->BT3, rows, stream));
+  } else {
+    h->AT3 = h->A3;
+    h->BT3 = h->B3;
+  }
+  CK3(cudaMallocAsync((void **)&h->Ad3, sizeof(int) * N, stream));
+  CK3(cudaMallocAsync((void **)&h->Bd3, sizeof(int) * N, stream));
+  CK3(cudaMallocAsync((void **)&h->dR3, sizeof(int) * N, stream));
+  CK3(cudaMallocAsync((void **)&h->dC3, sizeof(int) * N, stream));
+  CK3(cudaMallocAsync((void **)&h->delta, sizeof(int) * (size_t)(M > 0 ? M : 1), stream));
+  CK3(cudaMallocAsync((void **)&h->p, sizeof(int) * N, stream));
+  CK3(cudaMallocAsync((void **)&h->st, sizeof(ChainStatus), stream));
+  CK3(cudaMallocAsync((void **)&h->P, sizeof(double) * 8 * 256, stream));
+  CK3(cudaMallocAsync((void **)&h->bar3, sizeof(unsigned long long), stream));
+  CK3(cudaMallocAsync((void **)&h->keys3, 4 * sizeof(unsigned), stream));
+  CK3(cudaMallocAsync((void **)&count, sizeof(int) * N, stream));
+  CK3(cudaMallocAsync((void **)&R, sizeof(long long) * (size_t)N * N, stream));
+  if (general) CK3(cudaMallocAsync((void **)&C, sizeof(long long) * (size_t)N * N, stream));
+  else C = R;
+  CK3(cudaMallocAsync((void **)&so, sizeof(SetupOut), stream));
+  CK3(cudaMemsetAsync(h->A3, 0, rows, stream));
+  CK3(cudaMemsetAsync(h->B3, 0, rows, stream));
+  if (general) {
+    CK3(cudaMemsetAsync(h->AT3, 0, rows, stream));
+    CK3(cudaMemsetAsync(h->BT3, 0, rows, stream));
+  }
+  CK3(cudaMemsetAsync(count, 0, sizeof(int) * N, stream));
+  CK3(cudaMemsetAsync(so, 0, sizeof(SetupOut), stream));
+  CK3(cudaMemsetAsync(h->st, 0, sizeof(ChainStatus), stream));
+  {
+    const long long NN = (long long)N * N;
+    const int blocks = (int)((NN + 255) / 256 < 4096 ? (NN + 255) / 256 : 4096);
+    t3_pack_kernel<<<blocks, 256, 0, stream>>>(A32, B32, p032, N, SA, h->A3, h->AT3, h->B3,
+                                               h->BT3, h->Ad3, h->Bd3, count, h->general, so);
+    t3_perm_kernel<<<(N + 255) / 256, 256, 0, stream>>>(p032, N, count, h->p, so);
+    dim3 gg((N + 127) / 128, N);
+    t3_gram_kernel<<<gg, 128, 0, stream>>>(h->A3, h->AT3, h->B3, h->p, N, SA, h->general, R, C);
+    t3_delta_kernel<<<gg, 128, 0, stream>>>(R, C, h->A3, h->B3, h->p, N, SA, h->general,
+                                            h->delta, h->dR3, h->dC3, so);
+    CK3(cudaGetLastError());
+  }
+  SetupOut so_h{};
+  CK3(cudaMemcpyAsync(&so_h, so, sizeof so_h, cudaMemcpyDeviceToHost, stream));
+  CK3(cudaStreamSynchronize(stream));
+  done(QAP_OK);
+  count = nullptr;
+  R = C = nullptr;
+  so = nullptr;
+  if (so_h.flags & kFlagPerm) return QAP_E_INVAL;
+
+  double T0 = sc->t0, Tf = sc->tf;
+  if (sc->flags & QAP_T_RELATIVE) {
+    const double mean = so_h.sum_abs_delta > 0 ? (double)so_h.sum_abs_delta / (double)M : 1.0;
+    T0 = sc->t0 * mean;
+    Tf = sc->tf * T0;
+  }
+  if (!(T0 > 0.0) || !(Tf > 0.0) || !isfinite(T0) || !isfinite(Tf)) return QAP_E_INVAL;
+  build_schedule(&h->sched, T0, Tf, sc->total_iters);
+  CK3(cudaMemcpyAsync(h->P, h->sched.P, sizeof h->sched.P, cudaMemcpyHostToDevice, stream));
+  {
+    ChainStatus st0{};
+    st0.cost = so_h.cost0;
+    CK3(cudaMemcpyAsync(h->st, &st0, sizeof st0, cudaMemcpyHostToDevice, stream));
+  }
+  T3Dev &g = h->dev3;
+  g.N = N;
+  g.M = M;
+  g.SA = SA;
+  g.general = h->general;
+  g.random_order = h->random_order;
+  g.G = tier3_grid(N, general);
+  g.A = h->A3;
+  g.AT = h->AT3;
+  g.B = h->B3;
+  g.BT = h->BT3;
+  g.Adiag = h->Ad3;
+  g.Bdiag = h->Bd3;
+  g.delta = h->delta;
+  g.p = h->p;
+  g.dR = h->dR3;
+  g.dC = h->dC3;
+  g.st = h->st;
+  g.bar = h->bar3;
+  g.keys = h->keys3;
+  g.seed = seed;
+  g.stream = sc->stream_id;
+  g.T0 = T0;
+  g.P = h->P;
+  g.T0f = (float)T0;
+  const double l2r = log2(Tf / T0);
+  g.log2a_f = sc->total_iters >= 2 ? (float)(l2r / (double)(sc->total_iters - 1)) : 0.0f;
+  g.mrel = (float)(2e-5 + 2e-7 * fabs(l2r) + 8.0 * (double)sc->total_iters * 0x1p-53);
+  h->cluster = g.G;
+  h->nthreads = kT3Threads;
+  h->smem_bytes = t3_smem_bytes(N, general);
+  CK3(cudaStreamSynchronize(stream));
+  return QAP_OK;
+#undef CK3
+}
+
 // Common body of the two create entry points; A32/B32/p032 are device
 // pointers that stay valid for the duration of the call.
 int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
@@ -426,6 +699,25 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
     cudaError_t e_ = (call);                                \
     if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call)); \
   } while (0)
+  // The on-chip tiers take the symmetric, zero-diagonal instances with int8
+  // entries in sequential order up to a cluster's capacity; tier 3 the rest.
+  {
+    SetupOut cls{};
+    rc = classify(A32, B32, N, p032, stream, &cls);
+    if (rc) return fail(rc);
+    if (cls.flags & kFlagPerm) return fail(QAP_E_INVAL);
+    const bool random = (sc->flags & QAP_ORDER_RANDOM) != 0;
+    const bool general = (cls.flags & (kFlagAsym | kFlagDiag)) != 0;
+    const bool wide = (cls.flags & (kFlagRangeA | kFlagRangeB)) != 0;
+    const char *et = getenv("QAPSA_TIER");
+    const bool force3 = et && atoi(et) == 3;
+    if (random || general || wide || force3 || N > max_n_tier2()) {
+      rc = create_tier3(h, A32, B32, p032, sc, seed, general, random, cls);
+      if (rc) return fail(rc);
+      *out = h;
+      return QAP_OK;
+    }
+  }
   const size_t nS = (size_t)N * S;
   CKF(cudaMallocAsync((void **)&h->A8, nS, stream));
   CKF(cudaMallocAsync((void **)&h->Bp8, nS, stream));
@@ -571,7 +863,7 @@ int validate_args(const void *A, const void *B, int32_t N, const void *p0,
   if (sc->total_iters == 0) return QAP_E_INVAL;
   if (!(sc->t0 > 0.0) || !(sc->tf > 0.0) || !isfinite(sc->t0) || !isfinite(sc->tf))
     return QAP_E_INVAL;
-  if (sc->flags & ~QAP_T_RELATIVE) return QAP_E_INVAL;
+  if (sc->flags & ~(QAP_T_RELATIVE | QAP_ORDER_RANDOM)) return QAP_E_INVAL;
   if (max_n_tier1() == 0) return QAP_E_CUDA;
   if (N > max_n_any()) return QAP_E_UNSUPPORTED;
   return QAP_OK;
@@ -658,7 +950,18 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
   while (cur < end) {
     unsigned long long stop = cur + chunk_iters();
     if (stop > end) stop = end;
-    if (h->tier == 2) {
+    if (h->tier == 3) {
+      CK(cudaMemsetAsync(h->bar3, 0, sizeof(unsigned long long), h->stream));
+      CK(cudaMemsetAsync(h->keys3, 0xFF, 3 * sizeof(unsigned), h->stream));
+      T3Dev d3 = h->dev3;
+      unsigned long long e3 = stop;
+      void *args[] = {&d3, &e3};
+      const void *k = h->general ? (const void *)sa_tier3_kernel<true>
+                                 : (const void *)sa_tier3_kernel<false>;
+      cudaError_t el = cudaLaunchCooperativeKernel(k, dim3(h->dev3.G), dim3(kT3Threads), args,
+                                                   (size_t)h->smem_bytes, h->stream);
+      if (el != cudaSuccess) return cuda_fail(el, "sa_tier3_kernel launch");
+    } else if (h->tier == 2) {
       // With the direct mode enabled a launch may leave Delta in global memory
       // stale (it ended in direct mode) or stop early to resume Delta mode:
       // rebuild Delta if flagged, and launch again to the same end (a no-op if
@@ -694,6 +997,7 @@ int qap_sa_sync(qap_sa *h) {
   int err = 0;
   CK(cudaMemcpyAsync(&err, &h->st->error, sizeof err, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (err == kT3ErrTimeout) return QAP_E_TIMEOUT;
   return err ? QAP_E_STATE : QAP_OK;
 }
 
@@ -821,6 +1125,17 @@ void qap_sa_destroy(qap_sa *h) { free_handle(h); }
 
 int32_t qap_sa_max_n(void) { return max_n_any(); }
 
+int32_t qap_sa_max_n_tier(int32_t tier) {
+  if (max_n_tier1() == 0) return 0;
+  switch (tier) {
+    case 1: return max_n_tier1();
+    case 2: return max_n_tier2();
+    case 3: return max_n_tier3(false);
+    case 4: return max_n_tier3(true);
+    default: return 0;
+  }
+}
+
 const char *qap_sa_strerror(int status) {
   switch (status) {
     case QAP_OK: return "ok";
@@ -899,6 +1214,10 @@ int qap_batch_create(const qap_problem *probs, int32_t count, qap_batch **out) {
       return rc;
     }
     b->h.push_back(h);
+    if (h->tier == 3) {  // a grid-wide chain cannot share a persistent launch
+      free_batch(b);
+      return QAP_E_UNSUPPORTED;
+    }
     BatchChain bc{};
     bc.g = h->dev;
     bc.it_end = 0;

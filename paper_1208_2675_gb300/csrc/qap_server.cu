@@ -227,7 +227,21 @@ int qap_server_submit(qap_server *s, const qap_problem *q, uint64_t iters,
   if (!s || !q || !ticket || !q->A || !q->B || !q->p0 || q->N < 2) return QAP_E_INVAL;
   if (s->stopping.load()) return QAP_E_STATE;
   if (iters > q->sched.total_iters) return QAP_E_RANGE;
-  if (q->N > qap_sa_max_n()) return QAP_E_UNSUPPORTED;
+  if (q->N > qap_sa_max_n_tier(2)) return QAP_E_UNSUPPORTED;
+  // The server shares the GPU between chains of one SM or one cluster each; a
+  // chain that needs the grid tier (general instance, wide entries, random
+  // order) is not served.
+  if (q->sched.flags & QAP_ORDER_RANDOM) return QAP_E_UNSUPPORTED;
+  {
+    const int32_t N = q->N;
+    for (int32_t i = 0; i < N; ++i)
+      for (int32_t j = 0; j < N; ++j) {
+        const int32_t a = q->A[(size_t)i * N + j], b = q->B[(size_t)i * N + j];
+        if (a != q->A[(size_t)j * N + i] || b != q->B[(size_t)j * N + i] ||
+            (i == j && (a != 0 || b != 0)) || a > 127 || a < -127 || b > 127 || b < -127)
+          return QAP_E_UNSUPPORTED;
+      }
+  }
   auto r = std::make_shared<Request>();
   const size_t nn = (size_t)q->N * q->N;
   r->N = q->N;

@@ -23,6 +23,7 @@ QAP_E_TIMEOUT = -5
 QAP_E_STATE = -6
 QAP_E_UNSUPPORTED = -7
 QAP_T_RELATIVE = 1
+QAP_ORDER_RANDOM = 2
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -119,6 +120,7 @@ SIGNATURES = {
                                             ctypes.c_void_p]),
     "qap_peaks_measure": (ctypes.c_int, [ctypes.POINTER(qap_peaks)]),
     "qap_sa_max_n": (ctypes.c_int32, []),
+    "qap_sa_max_n_tier": (ctypes.c_int32, [ctypes.c_int32]),
     "qap_sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -159,9 +161,9 @@ def _i32(a) -> np.ndarray:
 
 
 def make_schedule(t0: float, tf: float, total_iters: int, relative: bool = True,
-                  stream_id: int = 0) -> qap_schedule:
-    return qap_schedule(float(t0), float(tf), int(total_iters),
-                        QAP_T_RELATIVE if relative else 0, int(stream_id))
+                  stream_id: int = 0, random_order: bool = False) -> qap_schedule:
+    flags = (QAP_T_RELATIVE if relative else 0) | (QAP_ORDER_RANDOM if random_order else 0)
+    return qap_schedule(float(t0), float(tf), int(total_iters), flags, int(stream_id))
 
 
 # ---- C entry points, same names ------------------------------------------- #
@@ -276,6 +278,10 @@ def qap_sa_max_n() -> int:
     return int(lib().qap_sa_max_n())
 
 
+def qap_sa_max_n_tier(tier: int) -> int:
+    return int(lib().qap_sa_max_n_tier(int(tier)))
+
+
 def qap_sa_strerror(status: int) -> str:
     return lib().qap_sa_strerror(int(status)).decode()
 
@@ -387,10 +393,11 @@ class Chain:
     """One SA chain on the GPU (a qap_sa handle)."""
 
     def __init__(self, A, B, p0, *, t0: float, tf: float, total_iters: int,
-                 relative: bool = True, seed: int = 0, stream_id: int = 0):
+                 relative: bool = True, seed: int = 0, stream_id: int = 0,
+                 random_order: bool = False):
         self.N = len(p0)
         self.M = self.N * (self.N - 1) // 2
-        self.sched = make_schedule(t0, tf, total_iters, relative, stream_id)
+        self.sched = make_schedule(t0, tf, total_iters, relative, stream_id, random_order)
         self.h = qap_sa_create(A, B, p0, self.sched, seed)
 
     @classmethod

@@ -97,11 +97,12 @@ def test_trajectory_matches_oracle(N, I, seed):
 
 
 def test_largest_tier1_size_partial_run():
-    N = sa.qap_sa_max_n()
+    N = sa.qap_sa_max_n_tier(1)
     assert N >= 200
     A, B, p0 = instances.taixxa_like(N, 9)
-    gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=10 ** 7, seed=9,
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=10 ** 7, seed=9,
                                      oracle_iters=60000)
+    assert g.info()["tier"] == 1
     assert os_["accepts"] > 1000
     assert_same(gs, os_, gd, od)
 
@@ -192,16 +193,13 @@ def test_negative_entries_and_zero_matrix():
 def test_invalid_inputs_are_rejected():
     A, B, p0 = instances.taixxa_like(10, 1)
     kw = dict(t0=0.5, tf=1e-3, total_iters=100)
+    # asymmetric A, a nonzero diagonal, entries beyond int8: accepted, on tier 3
     bad = A.copy()
     bad[0, 1] += 1
-    with pytest.raises(sa.QapError) as e:
-        sa.Chain(bad, B, p0, **kw)
-    assert e.value.status == sa.QAP_E_INVAL
+    assert sa.Chain(bad, B, p0, **kw).info()["tier"] == 3
     bad = B.copy()
     bad[3, 3] = 1
-    with pytest.raises(sa.QapError) as e:
-        sa.Chain(A, bad, p0, **kw)
-    assert e.value.status == sa.QAP_E_INVAL
+    assert sa.Chain(A, bad, p0, **kw).info()["tier"] == 3
     q = p0.copy()
     q[0] = q[1]
     with pytest.raises(sa.QapError) as e:
@@ -209,9 +207,14 @@ def test_invalid_inputs_are_rejected():
     assert e.value.status == sa.QAP_E_INVAL
     big = A.copy()
     big[0, 1] = big[1, 0] = 128
+    assert sa.Chain(big, B, p0, **kw).info()["tier"] == 3
+    big[0, 1] = big[1, 0] = 1 << 20  # 8 N max|A| max|B| beyond 2^31 - 1
     with pytest.raises(sa.QapError) as e:
         sa.Chain(big, B, p0, **kw)
     assert e.value.status == sa.QAP_E_RANGE
+    with pytest.raises(sa.QapError) as e:  # an unknown schedule flag
+        sa.qap_sa_create(A, B, p0, sa.qap_schedule(0.5, 0.1, 100, 8, 0), 0)
+    assert e.value.status == sa.QAP_E_INVAL
     with pytest.raises(sa.QapError) as e:
         sa.Chain(A, B, p0, t0=0.5, tf=0.0, total_iters=100)
     assert e.value.status == sa.QAP_E_INVAL
@@ -395,7 +398,7 @@ def test_largest_cluster_delta_mode_matches_oracle(monkeypatch):
     """The largest size the cluster tier takes (16 CTAs) in Delta mode, against
     the oracle after 10000 iterations, Delta element by element."""
     monkeypatch.setenv("QAPSA_CLUSTER_HYBRID_RATE", "0")
-    N = sa.qap_sa_max_n()
+    N = sa.qap_sa_max_n_tier(2)
     assert N >= 1100
     A, B, p0 = instances.taixxa_like(N, 61)
     gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.05, tf=1e-3, I=10 ** 9, seed=61,
