@@ -663,6 +663,14 @@ int create_tier3(qap_sa *h, const int32_t *A32, const int32_t *B32, const int32_
   h->cluster = g.G;
   h->nthreads = kT3Threads;
   h->smem_bytes = t3_smem_bytes(N, general);
+  // keep each CTA's share of rows in shared memory when it fits
+  g.nvmax = (N + g.G - 1) / g.G + 1;
+  g.cache_rows = 0;
+  if (!getenv("QAPSA_T3_NOCACHE") &&
+      h->smem_bytes + t3_cache_bytes(N, general, g.nvmax) + 64 <= device_smem_optin()) {
+    g.cache_rows = 1;
+    h->smem_bytes += t3_cache_bytes(N, general, g.nvmax);
+  }
   CK3(cudaStreamSynchronize(stream));
   return QAP_OK;
 #undef CK3

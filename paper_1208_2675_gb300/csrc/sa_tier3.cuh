@@ -70,6 +70,9 @@ struct T3Dev {
   double T0;
   const double *P;
   float T0f, log2a_f, mrel;
+  int cache_rows;        // this CTA's share of rows of A, B (A^T, B^T) kept in
+                         // shared memory for the rows-r,s recompute
+  int nvmax;             // rows in a share, at most
 };
 
 // Shared memory: vectors of NP int32 each, then the control block.
@@ -101,6 +104,10 @@ __host__ __device__ inline int t3_nvec(bool gen) { return gen ? (int)kV_count : 
 constexpr int kT3CtlBytes = 256;
 __host__ __device__ inline int t3_smem_bytes(int N, bool gen) {
   return t3_nvec(gen) * 4 * t3_np(N) + kT3CtlBytes;
+}
+// The cached rows: A_v, B_p(v) (and A^T_v, B^T_p(v)) for the nvmax rows v of a share.
+__host__ __device__ inline int t3_cache_bytes(int N, bool gen, int nvmax) {
+  return (gen ? 4 : 2) * nvmax * 4 * t3_np(N);
 }
 
 // Pair number m of the random order at iteration it: (x M) >> 32, x word 0 of
@@ -216,11 +223,30 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
   __syncthreads();
   for (int i = tid; i < N; i += kT3Threads) s_q[s_p[i]] = i;
   unsigned mbar_phase = 0;
+  const bool cache = g.cache_rows != 0;
+  int *s_RA = reinterpret_cast<int *>(ctl + kT3CtlBytes);  // [nvmax][NP] each
+  int *s_RB = s_RA + g.nvmax * NP;
+  int *s_RAT = GEN ? s_RB + g.nvmax * NP : s_RA;
+  int *s_RBT = GEN ? s_RAT + g.nvmax * NP : s_RB;
 
   // this CTA's cells and share of rows
   const long long Mll = M;
   const int lo = (int)((Mll * gb) / G), hi = (int)((Mll * (gb + 1)) / G);
   const int v_lo = (int)(((long long)N * gb) / G), v_hi = (int)(((long long)N * (gb + 1)) / G);
+  if (cache) {  // this CTA's share of rows, for the whole launch (B rows follow p)
+    __syncthreads();
+    for (int i = 0; i < v_hi - v_lo; ++i) {
+      const int v = v_lo + i, pv = s_p[v];
+      for (int k = tid; k < NP; k += kT3Threads) {
+        s_RA[i * NP + k] = __ldg(g.A + (size_t)v * SA + k);
+        s_RB[i * NP + k] = __ldg(g.B + (size_t)pv * SA + k);
+        if (GEN) {
+          s_RAT[i * NP + k] = __ldg(g.AT + (size_t)v * SA + k);
+          s_RBT[i * NP + k] = __ldg(g.BT + (size_t)pv * SA + k);
+        }
+      }
+    }
+  }
 
   unsigned long long it = g.st->it;
   unsigned long long accepts = g.st->accepts;
@@ -391,6 +417,16 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
     // the vectors of the O(1) update (k outside {r, s}: B' before the swap of
     // row r is B' after it of row s, and so on)
     for (int k = tid; k < NP; k += kT3Threads) {
+      if (cache) {  // rows r and s of the share now hold rows p'(r), p'(s) of B
+        if (r >= v_lo && r < v_hi) {
+          s_RB[(r - v_lo) * NP + k] = s_Br[k];
+          if (GEN) s_RBT[(r - v_lo) * NP + k] = s_BTr[k];
+        }
+        if (s >= v_lo && s < v_hi) {
+          s_RB[(s - v_lo) * NP + k] = s_Bs[k];
+          if (GEN) s_RBT[(s - v_lo) * NP + k] = s_BTs[k];
+        }
+      }
       if (k < N) {
         const int pk = s_p[k], qk = s_q[k];
         const int btr = s_Br[pk], bts = s_Bs[pk];
@@ -415,75 +451,72 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
       }
     }
     __syncthreads();
-    // ---- Gram diagonals: O(1) off r,s; d_R(r), d_R(s), d_C(r), d_C(s) by dot products ----
-    {
-      long long p1 = 0, p2 = 0, p3 = 0, p4 = 0;
-      for (int k = tid; k < N; k += kT3Threads) {
-        p1 += (long long)s_Ar[k] * s_Btr[k];
-        p2 += (long long)s_As[k] * s_Bts[k];
-        if (GEN) {
-          p3 += (long long)s_Acr[k] * s_Bcr[k];
-          p4 += (long long)s_Acs[k] * s_Bcs[k];
-        }
-        if (k != r && k != s) {
-          s_dR[k] += s_c[k] * s_e[k];
-          if (GEN) s_dC[k] += s_a[k] * s_b[k];
-        }
+    // ---- Gram diagonals (O(1) off r,s; warps 0-3 take the four dot products
+    //      of d_R(r), d_R(s), d_C(r), d_C(s)) and the O(1) update of this CTA's
+    //      cells off rows and columns r,s, eight loads in flight per thread ----
+    for (int k = tid; k < N; k += kT3Threads) {
+      if (k != r && k != s) {
+        s_dR[k] += s_c[k] * s_e[k];
+        if (GEN) s_dC[k] += s_a[k] * s_b[k];
       }
+    }
+    if (warp < (GEN ? 4 : 2)) {
+      const int *x = warp == 0 ? s_Ar : (warp == 1 ? s_As : (warp == 2 ? s_Acr : s_Acs));
+      const int *y = warp == 0 ? s_Btr : (warp == 1 ? s_Bts : (warp == 2 ? s_Bcr : s_Bcs));
+      long long acc = 0;
+      for (int k = lane; k < N; k += 32) acc += (long long)x[k] * y[k];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        p1 += __shfl_xor_sync(0xFFFFFFFFu, p1, off);
-        p2 += __shfl_xor_sync(0xFFFFFFFFu, p2, off);
-        p3 += __shfl_xor_sync(0xFFFFFFFFu, p3, off);
-        p4 += __shfl_xor_sync(0xFFFFFFFFu, p4, off);
-      }
-      if (tid < 4) s_sum[tid] = 0;
-      __syncthreads();
-      if (lane == 0) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(s_sum + 0), (unsigned long long)p1);
-        atomicAdd(reinterpret_cast<unsigned long long *>(s_sum + 1), (unsigned long long)p2);
-        if (GEN) {
-          atomicAdd(reinterpret_cast<unsigned long long *>(s_sum + 2), (unsigned long long)p3);
-          atomicAdd(reinterpret_cast<unsigned long long *>(s_sum + 3), (unsigned long long)p4);
-        }
-      }
-      __syncthreads();
-      if (tid == 0) {
-        s_dR[r] = (int)s_sum[0];
-        s_dR[s] = (int)s_sum[1];
-        if (GEN) {
-          s_dC[r] = (int)s_sum[2];
-          s_dC[s] = (int)s_sum[3];
-        }
-      }
-      __syncthreads();
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+      if (lane == 0) s_sum[warp] = acc;
     }
-    // ---- O(1) update of this CTA's cells off rows and columns r,s ----
     {
-      int m0 = lo + tid;
       int u = 0, vv = 0;
-      if (m0 < hi) decode_pair(N, m0, u, vv);
-      for (int mm = m0; mm < hi; mm += kT3Threads) {
-        while (mm >= t3_row_start(N, u + 1)) ++u;  // rows of this thread's cells ascend
-        const int v = mm - t3_row_start(N, u) + u + 1;
-        if (u == r || u == s || v == r || v == s) {
-          if (u == r && v == s) __stcg(g.delta + mm, -dlt);
-          continue;
+      if (lo + tid < hi) decode_pair(N, lo + tid, u, vv);
+      for (int base = lo + tid; base < hi; base += 8 * kT3Threads) {
+        int dl[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int mm = base + i * kT3Threads;
+          dl[i] = mm < hi ? __ldcg(g.delta + mm) : 0;
         }
-        int d = __ldcg(g.delta + mm);
-        d += (s_a[u] - s_a[v]) * (s_b[v] - s_b[u]);
-        d += (s_c[u] - s_c[v]) * (s_e[v] - s_e[u]);
-        __stcg(g.delta + mm, d);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int mm = base + i * kT3Threads;
+          if (mm >= hi) break;
+          while (mm >= t3_row_start(N, u + 1)) ++u;  // rows of this thread's cells ascend
+          const int v = mm - t3_row_start(N, u) + u + 1;
+          if (u == r || u == s || v == r || v == s) {
+            if (u == r && v == s) __stcg(g.delta + mm, -dlt);
+            continue;
+          }
+          int d = dl[i];
+          d += (s_a[u] - s_a[v]) * (s_b[v] - s_b[u]);
+          d += (s_c[u] - s_c[v]) * (s_e[v] - s_e[u]);  // symmetric: c = a, e = b
+          __stcg(g.delta + mm, d);
+        }
       }
     }
+    __syncthreads();
+    if (tid == 0) {
+      s_dR[r] = (int)s_sum[0];
+      s_dR[s] = (int)s_sum[1];
+      if (GEN) {
+        s_dC[r] = (int)s_sum[2];
+        s_dC[s] = (int)s_sum[3];
+      }
+    }
+    __syncthreads();
     // ---- cells (r, v) and (s, v) of this CTA's share of v: one warp a row ----
     for (int v = v_lo + warp; v < v_hi; v += kT3Warps) {
       if (v == r || v == s) continue;
       const int pv = s_p[v];
-      const int4 *Av = reinterpret_cast<const int4 *>(g.A + (size_t)v * SA);
-      const int4 *Bv = reinterpret_cast<const int4 *>(g.B + (size_t)pv * SA);
-      const int4 *ATv = reinterpret_cast<const int4 *>(g.AT + (size_t)v * SA);
-      const int4 *BTv = reinterpret_cast<const int4 *>(g.BT + (size_t)pv * SA);
+      const int iv = v - v_lo;
+      const int4 *Av = reinterpret_cast<const int4 *>(cache ? s_RA + iv * NP : g.A + (size_t)v * SA);
+      const int4 *Bv = reinterpret_cast<const int4 *>(cache ? s_RB + iv * NP : g.B + (size_t)pv * SA);
+      const int4 *ATv =
+          reinterpret_cast<const int4 *>(cache ? s_RAT + iv * NP : g.AT + (size_t)v * SA);
+      const int4 *BTv =
+          reinterpret_cast<const int4 *>(cache ? s_RBT + iv * NP : g.BT + (size_t)pv * SA);
       const int4 *atr = reinterpret_cast<const int4 *>(s_Atr);
       const int4 *ats = reinterpret_cast<const int4 *>(s_Ats);
       const int4 *btr = reinterpret_cast<const int4 *>(s_Btr);
@@ -494,7 +527,7 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
       const int4 *bcs = reinterpret_cast<const int4 *>(s_Bcs);
       int Rrv = 0, Rsv = 0, Rvr = 0, Rvs = 0, Crv = 0, Csv = 0, Cvr = 0, Cvs = 0;
       for (int c = lane; c < (NP >> 2); c += 32) {
-        const int4 bv = __ldg(Bv + c), av = __ldg(Av + c);
+        const int4 bv = cache ? Bv[c] : __ldg(Bv + c), av = cache ? Av[c] : __ldg(Av + c);
         int4 x = atr[c];
         Rrv += x.x * bv.x + x.y * bv.y + x.z * bv.z + x.w * bv.w;
         x = ats[c];
@@ -504,7 +537,8 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
         x = bts[c];
         Rvs += av.x * x.x + av.y * x.y + av.z * x.z + av.w * x.w;
         if (GEN) {
-          const int4 btv = __ldg(BTv + c), atv = __ldg(ATv + c);
+          const int4 btv = cache ? BTv[c] : __ldg(BTv + c);
+          const int4 atv = cache ? ATv[c] : __ldg(ATv + c);
           x = actr[c];
           Crv += x.x * btv.x + x.y * btv.y + x.z * btv.z + x.w * btv.w;
           x = acts[c];
