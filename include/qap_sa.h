@@ -319,6 +319,45 @@ QAP_EXPORT int qap_sa_setup_noalloc(const int32_t *A, const int32_t *B, int32_t 
                                     const int32_t *p, int32_t *delta_out,
                                     int64_t *cost_out, void *cuda_stream);
 
+/* ---- tuning ----------------------------------------------------------------
+ * The paper leaves the window ("subset") size as an adjustable parameter
+ * (section 3 (ii)); this library has more such knobs, none of which changes a
+ * trajectory: which tier runs a chain, when the swap cost of a proposal is read
+ * from Delta or evaluated directly, when one warp runs the direct mode alone,
+ * how many CTAs a grid-tier chain uses.  qap_tune measures them on the current
+ * GPU; qap_knobs_set makes a choice the default for a range of N.            */
+typedef struct qap_knobs {
+  int32_t tier;               /* 0: the default choice; 3: the grid tier even
+                                 where an on-chip tier could take the chain;
+                                 1 or 2: the on-chip tier for N's size (never
+                                 for instances only tier 3 can run)            */
+  int32_t t3_grid;            /* CTAs of a grid-tier chain (0: one per SM)     */
+  float hybrid_rate;          /* one SM: Delta maintained below this block
+                                 acceptance rate (< 0: the default 5e-4)       */
+  float warp_rate;            /* one SM: one warp runs the direct mode alone
+                                 from this rate (< 0: the default)             */
+  float cluster_hybrid_rate;  /* cluster: direct mode above this rate (< 0:
+                                 the default 2e-3; 0: Delta mode throughout)  */
+  uint32_t reserved;          /* must be 0                                     */
+} qap_knobs;
+
+/* Makes `k` the knobs of every chain created afterwards with n_lo <= N <= n_hi
+ * (a later call for an overlapping range takes precedence; k == NULL clears
+ * all ranges).  The QAPSA_* environment variables still override a knob.
+ * Process-wide and thread-safe.  QAP_E_INVAL for n_lo > n_hi or reserved != 0. */
+QAP_EXPORT int qap_knobs_set(int32_t n_lo, int32_t n_hi, const qap_knobs *k);
+
+/* Measures the candidate knobs for problems of size N on the current GPU and
+ * returns the fastest in *best (and its time in *seconds, may be NULL): each
+ * candidate runs the same seeded uniform symmetric instance (entries in
+ * [0, 99], zero diagonal) over a whole geometric schedule of `iters`
+ * iterations from T0 = 0.5 mean|Delta_0| to Tf = 1e-3 T0, the schedule form of
+ * the library's workloads.  Candidates: the grid tier against the on-chip one
+ * (N > 2), the direct/Delta switch rates of the on-chip tier, and for the grid
+ * tier one CTA per SM or half as many.  Blocks; takes a few times a run of
+ * `iters` iterations.  Errors as qap_sa_create.                               */
+QAP_EXPORT int qap_tune(int32_t N, uint64_t iters, qap_knobs *best, double *seconds);
+
 /* ---- library ------------------------------------------------------------- */
 /* Largest N any tier supports on the current device (0 if no device).      */
 QAP_EXPORT int32_t qap_sa_max_n(void);

@@ -17,6 +17,7 @@
 #include "sa_tier2.cuh"
 #include "sa_tier3.cuh"
 
+#include <chrono>
 #include <vector>
 
 using namespace qapsa;
@@ -54,6 +55,35 @@ unsigned long long chunk_iters() {
 // Set once by preload_kernels (see there).
 int g_tmem_min_smem = 0;   // least dynamic shared memory of a TMEM-kernel launch
 bool g_tmem_ok = true;     // one TMEM-holding CTA per SM is guaranteed
+
+// Knobs registered with qap_knobs_set (later ranges first), and the knobs of
+// qap_tune's trial chains on the calling thread.
+struct KnobRange {
+  int lo, hi;
+  qap_knobs k;
+};
+std::mutex g_knob_mu;
+std::vector<KnobRange> g_knobs;
+thread_local const qap_knobs *t_knob_override = nullptr;
+
+qap_knobs default_knobs() {
+  qap_knobs k{};
+  k.tier = 0;
+  k.t3_grid = 0;
+  k.hybrid_rate = -1.0f;
+  k.warp_rate = -1.0f;
+  k.cluster_hybrid_rate = -1.0f;
+  k.reserved = 0;
+  return k;
+}
+
+qap_knobs knobs_for(int N) {
+  if (t_knob_override) return *t_knob_override;
+  std::lock_guard<std::mutex> lock(g_knob_mu);
+  for (auto it = g_knobs.rbegin(); it != g_knobs.rend(); ++it)
+    if (it->lo <= N && N <= it->hi) return it->k;
+  return default_knobs();
+}
 
 int device_smem_optin() {
   int dev = 0, v = 0;
@@ -413,7 +443,7 @@ int max_n_any() {
 
 // CTAs of a tier-3 grid: one per SM, fewer for small problems (about 256 cells
 // of Delta each at least), within what a cooperative launch can keep resident.
-int tier3_grid(int N, bool general) {
+int tier3_grid(int N, bool general, int pref) {
   int dev = 0, sms = 1, nb = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -428,6 +458,7 @@ int tier3_grid(int N, bool general) {
   if (G < 1) G = 1;
   if (G > sms) G = sms;
   if (G > (long long)nb * sms) G = (long long)nb * sms;
+  if (pref >= 1 && pref <= (long long)nb * sms) G = pref;
   if (const char *e = getenv("QAPSA_T3_GRID")) {
     const long long x = atoll(e);
     if (x >= 1 && x <= (long long)nb * sms) G = x;
@@ -638,7 +669,7 @@ int create_tier3(qap_sa *h, const int32_t *A32, const int32_t *B32, const int32_
   g.SA = SA;
   g.general = h->general;
   g.random_order = h->random_order;
-  g.G = tier3_grid(N, general);
+  g.G = tier3_grid(N, general, knobs_for(N).t3_grid);
   g.A = h->A3;
   g.AT = h->AT3;
   g.B = h->B3;
@@ -718,7 +749,7 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
     const bool general = (cls.flags & (kFlagAsym | kFlagDiag)) != 0;
     const bool wide = (cls.flags & (kFlagRangeA | kFlagRangeB)) != 0;
     const char *et = getenv("QAPSA_TIER");
-    const bool force3 = et && atoi(et) == 3;
+    const bool force3 = et ? atoi(et) == 3 : knobs_for(N).tier == 3;
     if (random || general || wide || force3 || N > max_n_tier2()) {
       rc = create_tier3(h, A32, B32, p032, sc, seed, general, random, cls);
       if (rc) return fail(rc);
@@ -840,14 +871,18 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   // per proposal, eight proposals a pass).  Both from a sweep of whole runs at
   // N = 60..276; the modes change the speed only, never the trajectory.
   {
+    const qap_knobs kn = knobs_for(N);
     const char *e = getenv("QAPSA_HYBRID_RATE");
-    g.hyb_lo = (h->tier == 1) ? (e ? (float)atof(e) : 5e-4f) : 0.0f;
+    const float hdef = kn.hybrid_rate >= 0.0f ? kn.hybrid_rate : 5e-4f;
+    g.hyb_lo = (h->tier == 1) ? (e ? (float)atof(e) : hdef) : 0.0f;
     if (h->tier == 2) {  // the cluster tier: direct mode at high acceptance as well
       const char *ec = getenv("QAPSA_CLUSTER_HYBRID_RATE");
-      g.hyb_lo = ec ? (float)atof(ec) : 2e-3f;
+      const float cdef = kn.cluster_hybrid_rate >= 0.0f ? kn.cluster_hybrid_rate : 2e-3f;
+      g.hyb_lo = ec ? (float)atof(ec) : cdef;
     }
     const char *ew = getenv("QAPSA_WARP_RATE");
-    const float wdef = (h->nthreads <= kT1SmallThreads) ? 1.0f / 512.0f : 1.0f / 64.0f;
+    float wdef = (h->nthreads <= kT1SmallThreads) ? 1.0f / 512.0f : 1.0f / 64.0f;
+    if (kn.warp_rate >= 0.0f) wdef = kn.warp_rate;
     g.warp_lo = (h->tier == 1) ? (ew ? (float)atof(ew) : wdef) : 0.0f;
   }
   h->layout = t1_layout(N, S);
@@ -1132,6 +1167,112 @@ int qap_sa_accept_probe(qap_sa *h, int32_t n, const uint64_t *it, const uint64_t
 void qap_sa_destroy(qap_sa *h) { free_handle(h); }
 
 int32_t qap_sa_max_n(void) { return max_n_any(); }
+
+int qap_knobs_set(int32_t n_lo, int32_t n_hi, const qap_knobs *k) {
+  std::lock_guard<std::mutex> lock(g_knob_mu);
+  if (!k) {
+    g_knobs.clear();
+    return QAP_OK;
+  }
+  if (n_lo > n_hi || k->reserved != 0 || k->tier < 0 || k->tier > 3 || k->t3_grid < 0)
+    return QAP_E_INVAL;
+  g_knobs.push_back(KnobRange{n_lo, n_hi, *k});
+  return QAP_OK;
+}
+
+int qap_tune(int32_t N, uint64_t iters, qap_knobs *best, double *seconds) {
+  if (!best || N < 2 || iters < 1) return QAP_E_INVAL;
+  if (max_n_tier1() == 0) return QAP_E_CUDA;
+  if (N > max_n_any()) return QAP_E_UNSUPPORTED;
+  // the instance: uniform symmetric entries in [0, 99], zero diagonal, a random
+  // p0 (splitmix64 of a fixed seed: an input generator, nothing of the method)
+  uint64_t x = 0x9E3779B97F4A7C15ull ^ (uint64_t)N;
+  auto next = [&x]() {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  std::vector<int32_t> A((size_t)N * N, 0), B((size_t)N * N, 0), p0(N);
+  for (int i = 0; i < N; ++i)
+    for (int j = i + 1; j < N; ++j) {
+      A[(size_t)i * N + j] = A[(size_t)j * N + i] = (int32_t)(next() % 100);
+      B[(size_t)i * N + j] = B[(size_t)j * N + i] = (int32_t)(next() % 100);
+    }
+  for (int i = 0; i < N; ++i) p0[i] = i;
+  for (int i = N - 1; i > 0; --i) std::swap(p0[i], p0[(size_t)(next() % (uint64_t)(i + 1))]);
+  const qap_schedule sc{0.5, 1e-3, iters, QAP_T_RELATIVE, 0};
+  // candidates: the default choice first
+  std::vector<qap_knobs> cand;
+  cand.push_back(default_knobs());
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (N <= max_n_tier1()) {
+    const float hs[2] = {2.5e-4f, 1e-3f};
+    for (float hr : hs) {
+      qap_knobs k = default_knobs();
+      k.hybrid_rate = hr;
+      cand.push_back(k);
+    }
+    const float wdef = N <= 180 ? 1.0f / 512.0f : 1.0f / 64.0f;  // the defaults' scale
+    const float ws[2] = {0.5f * wdef, 2.0f * wdef};
+    for (float wr : ws) {
+      qap_knobs k = default_knobs();
+      k.warp_rate = wr;
+      cand.push_back(k);
+    }
+  } else if (N <= max_n_tier2()) {
+    const float cs[3] = {0.0f, 1e-3f, 4e-3f};
+    for (float cr : cs) {
+      qap_knobs k = default_knobs();
+      k.cluster_hybrid_rate = cr;
+      cand.push_back(k);
+    }
+  }
+  if (N > 2 && N <= max_n_tier2()) {
+    qap_knobs k = default_knobs();
+    k.tier = 3;
+    cand.push_back(k);
+    k.t3_grid = sms / 2 > 0 ? sms / 2 : 1;
+    cand.push_back(k);
+  } else if (N > max_n_tier2()) {
+    qap_knobs k = default_knobs();
+    k.t3_grid = sms / 2 > 0 ? sms / 2 : 1;
+    cand.push_back(k);
+  }
+  double best_s = 1e300;
+  int64_t cost0 = 0;
+  uint64_t acc0 = 0;
+  for (size_t c = 0; c < cand.size(); ++c) {
+    t_knob_override = &cand[c];
+    qap_sa *h = nullptr;
+    int rc = qap_sa_create(A.data(), B.data(), N, p0.data(), &sc, 1, &h);
+    t_knob_override = nullptr;
+    if (rc) return rc;
+    const auto t0 = std::chrono::steady_clock::now();
+    rc = qap_sa_run(h, iters);
+    const double dt =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int64_t cost = 0;
+    uint64_t acc = 0;
+    if (!rc) rc = qap_sa_result(h, nullptr, &cost, &acc);
+    qap_sa_destroy(h);
+    if (rc) return rc;
+    if (c == 0) {
+      cost0 = cost;
+      acc0 = acc;
+    } else if (cost != cost0 || acc != acc0) {
+      return QAP_E_STATE;  // a knob changed the trajectory: never expected
+    }
+    if (dt < best_s) {
+      best_s = dt;
+      *best = cand[c];
+    }
+  }
+  if (seconds) *seconds = best_s;
+  return QAP_OK;
+}
 
 int32_t qap_sa_max_n_tier(int32_t tier) {
   if (max_n_tier1() == 0) return 0;

@@ -14,6 +14,7 @@
 
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <deque>
 #include <memory>
 #include <mutex>
@@ -64,6 +65,14 @@ struct qap_server {
   std::atomic<bool> stopping{false};
   std::atomic<int> max_running{0};
   std::thread worker;
+  // admitted requests wait here for a set-up thread (under mu); set-up threads
+  // hand started chains to the worker through `started` (under mu)
+  std::deque<std::shared_ptr<Request>> setup_q;
+  std::vector<std::shared_ptr<Request>> started;
+  int in_setup = 0;             // admitted, not yet started or failed (under mu)
+  int head_bypassed = 0;        // requests admitted past a head that did not fit
+  std::condition_variable setup_cv;
+  std::vector<std::thread> setup_threads;
 };
 
 namespace {
@@ -120,10 +129,47 @@ bool launch(qap_server *s, const std::shared_ptr<Request> &r) {
   return true;
 }
 
+// Requests that may be admitted past a head waiting for SMs or memory, before
+// the head is waited for: small requests fill the gaps a cluster-sized head
+// leaves, and the head is not starved.
+constexpr int kMaxBypass = 32;
+constexpr int kSetupThreads = 4;
+
+// Set-up threads: create each admitted chain on its own stream and enqueue its
+// whole run, off the worker's path (a set-up waits for its kernels).
+void setup_main(qap_server *s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    std::shared_ptr<Request> r;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      s->setup_cv.wait(lock, [s] { return !s->setup_q.empty() || s->stopping.load(); });
+      if (s->setup_q.empty()) {
+        if (s->stopping.load()) return;
+        continue;
+      }
+      r = s->setup_q.front();
+      s->setup_q.pop_front();
+    }
+    const bool ok = launch(s, r);
+    std::lock_guard<std::mutex> lock(s->mu);
+    --s->in_setup;
+    if (ok) s->started.push_back(r);
+  }
+}
+
 void worker_main(qap_server *s) {
   cudaSetDevice(s->device);
   for (;;) {
     bool progress = false;
+    {  // chains the set-up threads have started
+      std::lock_guard<std::mutex> lock(s->mu);
+      for (auto &r : s->started) s->running.push_back(r);
+      if (!s->started.empty()) progress = true;
+      s->started.clear();
+    }
+    if ((int)s->running.size() > s->max_running.load())
+      s->max_running.store((int)s->running.size());
     // ---- completions ----
     for (size_t i = 0; i < s->running.size();) {
       const std::shared_ptr<Request> &r = s->running[i];
@@ -136,34 +182,55 @@ void worker_main(qap_server *s) {
       s->running.pop_back();
       progress = true;
     }
-    // ---- admissions: FIFO, as SMs and memory allow ----
-    for (;;) {
-      std::shared_ptr<Request> r;
-      {
-        std::lock_guard<std::mutex> lock(s->mu);
-        if (s->queue.empty()) break;
-        std::shared_ptr<Request> &head = s->queue.front();
-        const bool fits = s->sms_used + head->sms <= s->max_sms &&
-                          s->bytes_used + head->bytes <= s->budget;
-        if (!fits && !s->running.empty()) break;  // wait for a slot to free up
-        r = head;
-        s->queue.pop_front();
+    // ---- admissions: arrival order, as SMs and memory allow; while the head
+    //      waits for room, up to kMaxBypass later requests that fit may pass it ----
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      auto fits = [s](const Request &q) {
+        return s->sms_used + q.sms <= s->max_sms && s->bytes_used + q.bytes <= s->budget;
+      };
+      auto admit = [s](std::deque<std::shared_ptr<Request>>::iterator it) {
+        std::shared_ptr<Request> r = *it;
         s->sms_used += r->sms;
         s->bytes_used += r->bytes;
         r->t_start = Clock::now();
+        ++s->in_setup;
+        s->setup_q.push_back(r);
+        return s->queue.erase(it);
+      };
+      bool admitted = false;
+      while (!s->queue.empty()) {
+        Request &head = *s->queue.front();
+        const bool nothing_on_gpu = s->running.empty() && s->in_setup == 0;
+        if (fits(head) || nothing_on_gpu) {  // an oversize request runs alone
+          admit(s->queue.begin());
+          s->head_bypassed = 0;
+          admitted = true;
+          continue;
+        }
+        for (auto it = s->queue.begin() + 1;
+             it != s->queue.end() && s->head_bypassed < kMaxBypass;) {
+          if (fits(**it)) {
+            it = admit(it);
+            ++s->head_bypassed;
+            admitted = true;
+          } else {
+            ++it;
+          }
+        }
+        break;  // the head waits for a slot to free up
       }
-      if (launch(s, r)) {
-        s->running.push_back(r);
-        const int n = (int)s->running.size();
-        if (n > s->max_running.load()) s->max_running.store(n);
+      if (admitted) {
+        progress = true;
+        s->setup_cv.notify_all();
       }
-      progress = true;
     }
     if (!progress) {
       bool idle;
       {
         std::lock_guard<std::mutex> lock(s->mu);
-        idle = s->queue.empty() && s->running.empty();
+        idle = s->queue.empty() && s->running.empty() && s->in_setup == 0 &&
+               s->started.empty();
       }
       if (idle && s->stopping.load()) return;
       std::this_thread::sleep_for(std::chrono::microseconds(idle ? 200 : 20));
@@ -218,6 +285,7 @@ int qap_server_start(const qap_server_cfg *cfg, qap_server **out) {
     cudaGetLastError();
   }
   s->worker = std::thread(worker_main, s);
+  for (int k = 0; k < kSetupThreads; ++k) s->setup_threads.emplace_back(setup_main, s);
   *out = s;
   return QAP_OK;
 }
@@ -285,7 +353,13 @@ int qap_server_max_running(qap_server *s) { return s ? s->max_running.load() : 0
 int qap_server_stop(qap_server *s) {
   if (!s) return QAP_E_INVAL;
   s->stopping.store(true);
-  if (s->worker.joinable()) s->worker.join();
+  if (s->worker.joinable()) s->worker.join();  // returns once everything finished
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->setup_cv.notify_all();
+  }
+  for (auto &t : s->setup_threads)
+    if (t.joinable()) t.join();
   delete s;
   return QAP_OK;
 }

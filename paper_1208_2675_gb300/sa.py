@@ -59,6 +59,12 @@ class qap_peaks(ctypes.Structure):
                 ("smem_latency_ns", ctypes.c_double)]
 
 
+class qap_knobs(ctypes.Structure):
+    _fields_ = [("tier", ctypes.c_int32), ("t3_grid", ctypes.c_int32),
+                ("hybrid_rate", ctypes.c_float), ("warp_rate", ctypes.c_float),
+                ("cluster_hybrid_rate", ctypes.c_float), ("reserved", ctypes.c_uint32)]
+
+
 class qap_problem(ctypes.Structure):
     _fields_ = [("A", _i32p), ("B", _i32p), ("p0", _i32p), ("N", ctypes.c_int32),
                 ("reserved", ctypes.c_uint32), ("sched", qap_schedule),
@@ -119,6 +125,9 @@ SIGNATURES = {
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p]),
     "qap_peaks_measure": (ctypes.c_int, [ctypes.POINTER(qap_peaks)]),
+    "qap_knobs_set": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(qap_knobs)]),
+    "qap_tune": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(qap_knobs),
+                                ctypes.POINTER(ctypes.c_double)]),
     "qap_sa_max_n": (ctypes.c_int32, []),
     "qap_sa_max_n_tier": (ctypes.c_int32, [ctypes.c_int32]),
     "qap_sa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -272,6 +281,34 @@ def qap_peaks_measure() -> dict:
     out = {name: getattr(pk, name) for name, _ in qap_peaks._fields_}
     out["cluster_barrier_ns"] = dict(zip((2, 4, 8, 13, 16), list(pk.cluster_barrier_ns)))
     return out
+
+
+KNOB_FIELDS = [name for name, _ in qap_knobs._fields_ if name != "reserved"]
+
+
+def knobs_struct(d: dict | None) -> qap_knobs:
+    """A qap_knobs from a dict (missing fields: the defaults)."""
+    d = d or {}
+    return qap_knobs(int(d.get("tier", 0)), int(d.get("t3_grid", 0)),
+                     float(d.get("hybrid_rate", -1.0)), float(d.get("warp_rate", -1.0)),
+                     float(d.get("cluster_hybrid_rate", -1.0)), 0)
+
+
+def qap_knobs_set(n_lo: int, n_hi: int, knobs: dict | None) -> None:
+    """Registers knobs for N in [n_lo, n_hi]; knobs=None clears every range."""
+    if knobs is None:
+        _check(lib().qap_knobs_set(0, 0, None), "qap_knobs_set")
+    else:
+        k = knobs_struct(knobs)
+        _check(lib().qap_knobs_set(int(n_lo), int(n_hi), ctypes.byref(k)), "qap_knobs_set")
+
+
+def qap_tune(N: int, iters: int):
+    """(best knobs as a dict, seconds of the best trial run)."""
+    k = qap_knobs()
+    t = ctypes.c_double()
+    _check(lib().qap_tune(int(N), int(iters), ctypes.byref(k), ctypes.byref(t)), "qap_tune")
+    return {name: getattr(k, name) for name in KNOB_FIELDS}, t.value
 
 
 def qap_sa_max_n() -> int:
