@@ -170,6 +170,9 @@ typedef struct qap_sa_info {
                              above 1/512, or 1/64 for N above ~180)        */
   int32_t ctas;           /* CTAs (= SMs) the chain holds while it runs     */
   int32_t threads;        /* threads per CTA of the SA kernel               */
+  uint64_t hot_iters;     /* iterations run by the hot-phase kernel of the
+                             cluster tier (one SM, rows of A and B' in L2)
+                             while the acceptance rate was high            */
 } qap_sa_info;
 QAP_EXPORT int qap_sa_get_info(qap_sa *h, qap_sa_info *out);
 

@@ -16,6 +16,7 @@
 #include "qap_internal.h"
 #include "sa_tier2.cuh"
 #include "sa_tier3.cuh"
+#include "sa_hot.cuh"
 
 #include <chrono>
 #include <vector>
@@ -216,6 +217,14 @@ struct qap_sa {
   int smem_bytes = 0;   // dynamic shared memory of the SA kernel
   unsigned long long it_host = 0;  // iterations enqueued so far
   int tier = 1;
+  // tier 2: the hot-phase kernel (one CTA of hot_warps warps, rows in L2) runs
+  // each piece first while the chain's acceptance is at least hot_lo
+  int hot = 0;
+  int8_t *B8 = nullptr;  // B as int8 rows of stride S (the hot-phase kernel's)
+  int hot_warps = 0;
+  int hot_depth = 0;
+  int hot_smem = 0;
+  float hot_lo = 0.0f;
   // tier 3 (a persistent grid, Delta in global memory)
   int general = 0;                 // the general (asymmetric) swap-cost forms
   int random_order = 0;            // proposals drawn at random
@@ -248,6 +257,7 @@ void free_handle(qap_sa *h) {
   dfree(h->st, st);
   dfree(h->P, st);
   dfree(h->tiles, st);
+  dfree(h->B8, st);
   dfree(h->A3, st);
   if (h->AT3 != h->A3) dfree(h->AT3, st);
   dfree(h->B3, st);
@@ -307,6 +317,8 @@ void preload_kernels() {
     cudaFuncGetAttributes(&a, setup_delta_kernel);
     cudaFuncGetAttributes(&a, rebuild_delta_kernel);
     cudaFuncGetAttributes(&a, clear_rebuild_kernel);
+    cudaFuncGetAttributes(&a, hot_bprime_kernel);
+    cudaFuncGetAttributes(&a, hot_pack_b_kernel);
     cudaFuncGetAttributes(&a, classify_kernel);
     cudaFuncGetAttributes(&a, t3_pack_kernel);
     cudaFuncGetAttributes(&a, t3_perm_kernel);
@@ -326,6 +338,7 @@ void preload_kernels() {
     give_all((const void *)sa_batch_kernel);
     give_all((const void *)sa_tier2_kernel);
     give_all((const void *)sa_tier2_batch_kernel);
+    give_all((const void *)sa_hot_kernel);
     give_all((const void *)sa_tier3_kernel<false>);
     give_all((const void *)sa_tier3_kernel<true>);
     cudaFuncSetAttribute(sa_tier2_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -608,7 +621,8 @@ int create_tier3(qap_sa *h, const int32_t *A32, const int32_t *B32, const int32_
   CK3(cudaMallocAsync((void **)&h->Bd3, sizeof(int) * N, stream));
   CK3(cudaMallocAsync((void **)&h->dR3, sizeof(int) * N, stream));
   CK3(cudaMallocAsync((void **)&h->dC3, sizeof(int) * N, stream));
-  CK3(cudaMallocAsync((void **)&h->delta, sizeof(int) * (size_t)(M > 0 ? M : 1), stream));
+  // two copies of Delta: the state, and the buffer a swap writes during a launch
+  CK3(cudaMallocAsync((void **)&h->delta, 2 * sizeof(int) * (size_t)(M > 0 ? M : 1), stream));
   CK3(cudaMallocAsync((void **)&h->p, sizeof(int) * N, stream));
   CK3(cudaMallocAsync((void **)&h->st, sizeof(ChainStatus), stream));
   CK3(cudaMallocAsync((void **)&h->P, sizeof(double) * 8 * 256, stream));
@@ -677,6 +691,7 @@ int create_tier3(qap_sa *h, const int32_t *A32, const int32_t *B32, const int32_
   g.Adiag = h->Ad3;
   g.Bdiag = h->Bd3;
   g.delta = h->delta;
+  g.delta2 = h->delta + (M > 0 ? M : 1);
   g.p = h->p;
   g.dR = h->dR3;
   g.dC = h->dC3;
@@ -867,8 +882,8 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
   // costs as much as evaluating ~2000 proposals directly.  Above warp_lo one
   // warp evaluates them alone (windows of 32..128, no block barrier per
   // accepted swap): from 1 accept in 512 proposals for the 256-thread kernel
-  // (one lane per proposal), from 1 in 64 for the 640-thread one (four lanes
-  // per proposal, eight proposals a pass).  Both from a sweep of whole runs at
+  // (one lane per proposal), from 1 in 64 for the 640-thread one (two lanes
+  // per proposal, sixteen proposals a pass).  Both from a sweep of whole runs at
   // N = 60..276; the modes change the speed only, never the trajectory.
   {
     const qap_knobs kn = knobs_for(N);
@@ -884,6 +899,31 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
     float wdef = (h->nthreads <= kT1SmallThreads) ? 1.0f / 512.0f : 1.0f / 64.0f;
     if (kn.warp_rate >= 0.0f) wdef = kn.warp_rate;
     g.warp_lo = (h->tier == 1) ? (ew ? (float)atof(ew) : wdef) : 0.0f;
+    // The cluster tier's hot phase on one SM while at least hot_lo of the
+    // proposals are accepted, on as many warps (up to the default) as the
+    // staged rows leave room for.
+    if (h->tier == 2) {
+      const char *eh = getenv("QAPSA_HOT");
+      const char *el = getenv("QAPSA_HOT_RATE");
+      const char *ewp = getenv("QAPSA_HOT_WARPS");
+      const char *edp = getenv("QAPSA_HOT_DEPTH");
+      h->hot_lo = el ? (float)atof(el) : kHotRateDefault;
+      int W = ewp ? atoi(ewp) : kHotWarpsDefault;
+      W = W < 1 ? 1 : (W > kHotMaxWarps ? kHotMaxWarps : W);
+      int D = edp ? atoi(edp) : kHotDepthDefault;
+      D = D < 1 ? 1 : (D > 4 ? 4 : D);
+      while (W > 1 && hot_layout(N, S, W, D).bytes > device_smem_optin()) --W;
+      h->hot_warps = W;
+      h->hot_depth = D;
+      h->hot_smem = hot_layout(N, S, W, D).bytes;
+      h->hot = (eh ? atoi(eh) != 0 : true) && h->hot_lo > 0.0f && g.hyb_lo > 0.0f &&
+               h->hot_smem <= device_smem_optin();
+      if (h->hot) {
+        CKF(cudaMallocAsync((void **)&h->B8, (size_t)N * S, stream));
+        hot_pack_b_kernel<<<dim3((S + 255) / 256, N), 256, 0, stream>>>(B32, N, S, h->B8);
+        CKF(cudaGetLastError());
+      }
+    }
   }
   h->layout = t1_layout(N, S);
   h->smem_bytes = h->tier == 1 ? h->layout.bytes : tier2_bytes(N, h->cluster);
@@ -1011,6 +1051,16 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
       // the first launch got there).  The second launch starts in Delta mode or
       // at the end, so it never stops early.
       const int rounds = h->dev.hyb_lo > 0.0f ? 2 : 1;
+      if (h->hot && h->dev.hyb_lo > 0.0f) {
+        // the hot phase first (it returns at once after it has handed the
+        // chain over); it leaves B' and Delta in global memory to be rebuilt
+        sa_hot_kernel<<<1, 32 * h->hot_warps, h->hot_smem, h->stream>>>(h->dev, h->B8, stop,
+                                                                          h->hot_lo,
+                                                                          h->hot_depth);
+        hot_bprime_kernel<<<dim3((h->S + 255) / 256, h->N), 256, 0, h->stream>>>(h->dev, h->B8);
+        rebuild_delta_kernel<<<dim3((h->N + 127) / 128, h->N), 128, 0, h->stream>>>(h->dev);
+        clear_rebuild_kernel<<<1, 1, 0, h->stream>>>(h->st);
+      }
       for (int k = 0; k < rounds; ++k) {
         cudaError_t e2 = launch_tier2(h->dev, stop, h->cluster, h->smem_bytes, h->stream);
         if (e2 != cudaSuccess) return cuda_fail(e2, "sa_tier2_kernel launch");
@@ -1104,6 +1154,7 @@ int qap_sa_get_info(qap_sa *h, qap_sa_info *out) {
   out->warp_iters = st.warp_iters;
   out->ctas = h->cluster;
   out->threads = h->nthreads;
+  out->hot_iters = st.hot_iters;
   return st.error ? QAP_E_STATE : QAP_OK;
 }
 

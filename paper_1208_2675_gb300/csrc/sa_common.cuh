@@ -37,7 +37,12 @@ struct ChainStatus {
   unsigned long long warp_iters;      // direct iterations run by one warp alone
   int need_rebuild;                   // Delta in global memory is stale (cluster
                                       // tier after direct mode): rebuild it
-  int pad_;
+  int hot_off;                        // the hot-phase kernel has handed the chain
+                                      // over for good (acceptance fell below its rate)
+  unsigned long long hot_iters;       // iterations run by the hot-phase kernel
+  int need_bprime;                    // B' in global memory is stale (after the
+                                      // hot-phase kernel): B' = B[p][p] first
+  int pad3_;
   unsigned long long near_log[kNearLog];  // iterations of the first near-ties
   unsigned near_log_n;                    // near-ties logged (may exceed kNearLog)
   unsigned pad2_;

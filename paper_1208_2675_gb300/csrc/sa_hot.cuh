@@ -1,0 +1,412 @@
+// sa_hot.cuh -- the hot phase of a cluster-tier chain (Paul, arXiv:1208.2675,
+// sections 2.2 and 3): while many proposals are accepted, one CTA on one SM
+// evaluates them directly from the constant matrices A and B and the
+// permutation p, and maintains B' = B[p][p] (Eq. 3) only for the row it is
+// sweeping.
+//
+// The cluster kernel pays two cluster barriers and an exchange of rows over
+// distributed shared memory for every accepted swap, and a chain that keeps B'
+// in memory writes two bytes into every row of B' per accepted swap.  Both set
+// the pace while one proposal in three to one in a few hundred is accepted.
+// This kernel reads the swap cost of proposal (r, s) as
+//   delta = 2 (<A~_r, B_p(s)> + <A_s, B'_r> - d_r - d_s + 2 A_rs B'_rs),
+//   A~_r[m] = A[r][q(m)] (q = p^-1), so <A~_r, B_p(s)> = <A_r, B'_s>,
+//   B'_r[k] = B[p(r)][p(k)],  d_v = <A_v, B'_v>,
+// with A~_r, B'_r, A_r, d, p, q in shared memory.  The proposals of the cyclic
+// order run along row r (s = r+1 .. N-1) before moving to row r+1, so A~_r and
+// B'_r serve a whole row; each proposal needs rows A_s and B_p(s) of the
+// constant matrices, which the kernel streams from global memory (L2) with
+// cp.async into a ring of shared-memory slots a few passes ahead.  A staged row stays
+// valid across accepted swaps of its row sweep: an accepted (r, s*) changes p
+// only at r and s*, and the rows still to come have s > s*.
+//
+//   pass    group g (eight lanes; four groups a warp) takes proposal s of the
+//           window [s_cur, s_cur + K) with s = g mod P (P = 4 W): its rows
+//           are in slot s mod (D+1)P, and it keeps the copies of s + P .. s + DP
+//           issued (D passes ahead, so that a row is asked for a few passes
+//           before it is read), and draws the Philox word of its proposal and
+//           forms the binary32 interval for Eq. (2).  The first accepted (or
+//           undecided) proposal in sequential order: redux.min per warp, one
+//           CTA barrier.
+//   accept  (r, s*), from the staged rows of s*: d_k += (A_rk - A_s*k)(B'_s*k
+//           - B'_rk) off r, s*; the new B'_r (a gather of B_p(s*) by the new p)
+//           into the second buffer; d_r, d_s* by a reduction; two entries of
+//           A~_r; then p, q.  One CTA barrier.
+//   row     A_r, B_p(r) copied in, A~_r and B'_r gathered through q and p.
+//
+// Delta and B' in global memory are not maintained: the kernel flags both for
+// the host's kernels (B' = B[p][p], then Delta) before the cluster kernel
+// resumes.  It runs blocks of kHybBlock iterations and hands the chain over
+// for good at the end of the first block whose acceptance rate is below
+// hot_lo (below the cluster tier's switch rate g.hyb_lo, in Delta mode).  The
+// trajectory is the sequential method's: the same proposals, the same
+// decisions.  Symmetric instances with zero diagonals only (the cluster tier's).
+#pragma once
+#include "sa_tier1.cuh"
+
+namespace qapsa {
+
+constexpr int kHotPPW = 4;        // proposals (groups) per warp
+constexpr int kHotLPP = 8;        // lanes per proposal
+constexpr int kHotMaxWarps = 16;
+constexpr int kHotWarpsDefault = 8;
+constexpr int kHotDepthDefault = 2;  // passes the row copies run ahead
+// Acceptance rate below which the hot-phase kernel hands a chain over to the
+// cluster kernel (whose own switch to Delta mode is at g.hyb_lo).
+// From whole-piece timings of the N = 1024 schedule: per 1e8 iterations the
+// hot kernel takes 17.6 s against the cluster kernel's 30.9 s at acceptance
+// 0.05 and 11.1 s against 13.7 s at 0.019; the lines cross near 0.013.
+constexpr float kHotRateDefault = 0.012f;
+
+struct HotLayout {
+  int off_p, off_q, off_d;                      // int32 vectors
+  int off_Ar, off_At, off_Bt0, off_Bt1, off_Br; // int8 rows of S bytes
+  int off_key, off_slot, off_red, off_ctl;
+  int off_ring;                                 // (D+1)P slots of (A_s, B_p(s))
+  int bytes;
+};
+
+__host__ __device__ inline HotLayout hot_layout(int N, int S, int W, int D) {
+  HotLayout L;
+  const int NP = t1_vec_len(N);
+  const int P = kHotPPW * W;
+  int o = 0;
+  L.off_p = o;    o += 4 * NP;
+  L.off_q = o;    o += 4 * NP;
+  L.off_d = o;    o += 4 * NP;
+  L.off_Ar = o;   o += S;
+  L.off_At = o;   o += S;
+  L.off_Bt0 = o;  o += S;
+  L.off_Bt1 = o;  o += S;
+  L.off_Br = o;   o += S;
+  L.off_key = o;  o += 4 * 2 * kHotMaxWarps;
+  L.off_slot = o; o += 8 * 2 * kHotMaxWarps;
+  L.off_red = o;  o += 8 * kHotMaxWarps;
+  L.off_ctl = o;  o += 16;
+  o = align16(o);
+  L.off_ring = o; o += (D + 1) * P * 2 * S;
+  L.bytes = o;
+  return L;
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+// All but the most recent group of the calling thread's copies are complete.
+__device__ __forceinline__ void cp_async_wait_prior() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// g: the chain (A with rows of stride S; g.Bp, g.delta not used); B8: the
+// constant B with rows of stride S; hot_lo: the acceptance rate below which
+// the kernel hands the chain over; D >= 1: passes the row copies run ahead.
+// One CTA of 32 W threads (W <= kHotMaxWarps) with hot_layout(N, S, W, D).bytes
+// of dynamic shared memory.
+__global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
+    sa_hot_kernel(ChainDev g, const int8_t *__restrict__ B8, unsigned long long it_end,
+                  float hot_lo, int D) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  {
+    const ChainStatus *st = g.st;
+    if (g.hyb_lo <= 0.0f || hot_lo <= 0.0f || st->mode == 0 || st->hot_off || st->error ||
+        st->it >= it_end)
+      return;
+  }
+  const unsigned FULL = 0xFFFFFFFFu;
+  const int N = g.N, S = g.S, M = g.M, NC = S >> 4;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthreads = blockDim.x, W = nthreads >> 5;
+  const int P = kHotPPW * W;  // proposals a pass covers at most
+  const int R = (D + 1) * P;  // ring slots
+  const HotLayout L = hot_layout(N, S, W, D);
+  int *s_p = reinterpret_cast<int *>(smem + L.off_p);
+  int *s_q = reinterpret_cast<int *>(smem + L.off_q);
+  int *s_d = reinterpret_cast<int *>(smem + L.off_d);
+  int8_t *s_Ar = reinterpret_cast<int8_t *>(smem + L.off_Ar);  // A_r
+  int8_t *s_At = reinterpret_cast<int8_t *>(smem + L.off_At);  // A~_r
+  int8_t *s_Bt = reinterpret_cast<int8_t *>(smem + L.off_Bt0); // B'_r (current buffer)
+  int8_t *s_Bn = reinterpret_cast<int8_t *>(smem + L.off_Bt1); // B'_r (next buffer)
+  int8_t *s_Br = reinterpret_cast<int8_t *>(smem + L.off_Br);  // B_p(r)
+  unsigned *s_key = reinterpret_cast<unsigned *>(smem + L.off_key);
+  int2 *s_slot = reinterpret_cast<int2 *>(smem + L.off_slot);
+  int2 *s_red = reinterpret_cast<int2 *>(smem + L.off_red);
+  int *s_dec = reinterpret_cast<int *>(smem + L.off_ctl);
+  int8_t *s_ring = reinterpret_cast<int8_t *>(smem + L.off_ring);
+  const int8_t *gA = g.A;
+
+  const int NP = t1_vec_len(N);
+  for (int i = tid; i < NP; i += nthreads) {
+    s_p[i] = i < N ? g.p[i] : 0;
+    s_d[i] = i < N ? g.d[i] : 0;
+  }
+  for (int k = N + tid; k < S; k += nthreads) s_Bn[k] = 0;  // padding of the second buffer
+  __syncthreads();
+  for (int i = tid; i < N; i += nthreads) s_q[s_p[i]] = i;
+
+  unsigned long long it = g.st->it;
+  const unsigned long long it_start = it;
+  int r, s_cur;  // the row being swept and the next proposal's column
+  decode_pair(N, (int)(it % (unsigned long long)M), r, s_cur);
+  // thread 0's counters
+  unsigned long long n_acc = 0, n_pass = 0, n_exact = 0, n_near = 0;
+  long long d_cost = 0;
+  int blk_it = 0, blk_acc = 0, mode = 1, err = 0;
+  bool handover = false;
+  unsigned par = 0;
+  int K = min(32, P);  // proposals evaluated in a pass (adapted like a window)
+  int dR = 0;          // d_r of the row being swept
+  const int grp = lane >> 3, sub = lane & (kHotLPP - 1);
+  const int G = warp * kHotPPW + grp;  // this group's residue of s mod P
+  int nx = 0;                          // the group's next s not yet issued
+
+  // copies of the rows of proposal s into its slot (by the eight lanes of its group)
+  auto issue = [&](int s) {
+    int8_t *dst = s_ring + (size_t)(s % R) * (2 * S);
+    const int8_t *srcA = gA + (size_t)s * S;
+    const int8_t *srcB = B8 + (size_t)s_p[s] * S;
+    for (int c = sub; c < NC; c += kHotLPP) {
+      cp_async16(dst + 16 * c, srcA + 16 * c);
+      cp_async16(dst + S + 16 * c, srcB + 16 * c);
+    }
+  };
+  bool new_row = true;
+
+  while (it < it_end) {
+    if (new_row) {
+      // ================= start of row r at column s_cur =================
+      __syncthreads();  // A~_r, B'_r, p, q and the slots of the previous row settled
+      const int8_t *ra = gA + (size_t)r * S;
+      const int8_t *rb = B8 + (size_t)s_p[r] * S;
+      for (int c = tid; c < 2 * NC; c += nthreads) {
+        if (c < NC) cp_async16(s_Ar + 16 * c, ra + 16 * c);
+        else cp_async16(s_Br + 16 * (c - NC), rb + 16 * (c - NC));
+      }
+      // this group's first proposal of the row and the D after it
+      const int s0 = s_cur + ((G - s_cur % P) % P + P) % P;
+      for (nx = s0; nx <= s0 + D * P && nx < N; nx += P) issue(nx);
+      nx = s0 + (D + 1) * P;
+      cp_async_commit();
+      cp_async_wait_all();
+      __syncthreads();
+      for (int k = tid; k < S; k += nthreads) {
+        s_At[k] = k < N ? s_Ar[s_q[k]] : (int8_t)0;
+        s_Bt[k] = k < N ? s_Br[s_p[k]] : (int8_t)0;
+      }
+      dR = s_d[r];
+      new_row = false;
+      __syncthreads();
+    }
+    // ================= one pass: proposals s_cur .. s_cur + plen - 1 =================
+    const int plen = (int)min((unsigned long long)min(K, N - s_cur), it_end - it);
+    const int sg = s_cur + ((G - s_cur % P) % P + P) % P;  // this group's proposal
+    const int j = sg - s_cur;                                // its offset in the pass
+    const bool live = j < plen;
+    // keep the group's next D proposals staged
+    while (nx <= sg + D * P && nx < N) {
+      issue(nx);
+      nx += P;
+    }
+    cp_async_commit();
+    // Eq. (2) interval of this proposal, and d_s
+    float2 bnd = make_float2(0.0f, 0.0f);
+    int dsg = 0;
+    if (live && sub == 0) {
+      const unsigned long long itc = it + (unsigned)j;
+      const uint4 x = rng_block(g.seed, g.stream, itc >> 2);
+      const float Tc = g.T0f * exp2f(u64_to_f32(itc) * g.log2a_f);
+      bnd = accept_interval(g.mrel, Tc, word_of(x, (int)(itc & 3u)));
+      dsg = s_d[sg];
+    }
+    cp_async_wait_prior();  // the copies of proposal sg (issued a pass or more ago)
+    __syncwarp();
+    int g1 = 0, g2 = 0;
+    if (live) {
+      const int8_t *slot = s_ring + (size_t)(sg % R) * (2 * S);
+      const int4 *As4 = reinterpret_cast<const int4 *>(slot);
+      const int4 *Bs4 = reinterpret_cast<const int4 *>(slot + S);
+      const int4 *At4 = reinterpret_cast<const int4 *>(s_At);
+      const int4 *Bt4 = reinterpret_cast<const int4 *>(s_Bt);
+#pragma unroll 3
+      for (int c = sub; c < NC; c += kHotLPP) {
+        g1 = dot16x(At4[c], Bs4[c], g1);  // <A~_r, B_p(s)> = <A_r, B'_s>
+        g2 = dot16x(As4[c], Bt4[c], g2);  // <A_s, B'_r>
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < kHotLPP; o <<= 1) {
+      g1 += __shfl_xor_sync(FULL, g1, o);
+      g2 += __shfl_xor_sync(FULL, g2, o);
+    }
+    unsigned best = kNone;
+    int dv = 0;
+    if (live && sub == 0) {
+      dv = 2 * (g1 + g2 - dR - dsg + 2 * (int)s_Ar[sg] * (int)s_Bt[sg]);
+      const float df = (float)dv;
+      unsigned acc = 0, unc = 0;
+      if (dv <= 0 || df < bnd.x) acc = 1u;
+      else if (!(df > bnd.y)) unc = 1u;
+      if (acc | unc) best = ((unsigned)j << 1) | unc;
+    }
+    const unsigned wmin = __reduce_min_sync(FULL, best);
+    if (best != kNone && best == wmin) s_slot[par * kHotMaxWarps + warp] = make_int2(sg, dv);
+    if (lane == 0) s_key[par * kHotMaxWarps + warp] = wmin;
+    __syncthreads();  // keys and slots (and thread 0's d, p, q of the last swap)
+    const unsigned code =
+        __reduce_min_sync(FULL, lane < W ? s_key[par * kHotMaxWarps + lane] : kNone);
+    const unsigned pp = par;
+    par ^= 1u;
+    if (tid == 0) ++n_pass;
+
+    if (code == kNone) {
+      it += (unsigned)plen;
+      s_cur += plen;
+      blk_it += plen;
+      K = min(2 * K, P);
+    } else {
+      const int jw = (int)(code >> 1);
+      const int s_old = s_cur;
+      // the winner's warp: its group is (s_old + jw) mod P
+      const int2 sl = s_slot[pp * kHotMaxWarps + ((s_old + jw) % P) / kHotPPW];
+      const int ss = sl.x, dlt = sl.y;
+      bool take = true;
+      if (code & 1u) {  // undecided by the binary32 pre-test: binary64
+        if (tid == 0) {
+          ++n_exact;
+          *s_dec = exact_accept(g.seed, g.stream, g.T0, g.P, dlt, it + (unsigned)jw, &n_near,
+                                g.st);
+        }
+        __syncthreads();
+        take = *s_dec != 0;
+      }
+      if (ss != s_old + jw || ss <= r || ss >= N) {
+        err = 1;
+        break;
+      }
+      it += (unsigned)jw + 1;
+      s_cur = ss + 1;
+      blk_it += jw + 1;
+      if (take) {
+        // ================= accept the swap (r, ss) =================
+        if (jw < K / 8) K = max(4, K / 2);
+        ++blk_acc;
+        if (tid == 0) {
+          ++n_acc;
+          d_cost += dlt;
+        }
+        const int8_t *slot = s_ring + (size_t)(ss % R) * (2 * S);
+        const int8_t *As = slot, *Bps = slot + S;  // A_ss and B_p(ss)
+        const int pr = s_p[r], ps = s_p[ss];
+        int dr_part = 0, ds_part = 0;
+#pragma unroll 4
+        for (int k = tid; k < N; k += nthreads) {
+          const int pk = s_p[k];
+          const bool off = k != r && k != ss;
+          // the new B'_r[k] = B[p'(r)][p'(k)], p'(r) = p(ss), p' = p swapped at r, ss
+          const int gk = Bps[off ? pk : (k == r ? ps : pr)];
+          s_Bn[k] = (int8_t)gk;
+          const int ark = s_Ar[k], ask = As[k];
+          // the new B'_ss[k] = B[p(r)][p'(k)]: the old B'_r at k with r, ss exchanged
+          const int bto = s_Bt[off ? k : (k == r ? ss : r)];
+          dr_part += ark * gk;
+          ds_part += ask * bto;
+          if (off) s_d[k] += (ark - ask) * (gk - (int)s_Bt[k]);  // the old B'_ss,k is gk here
+        }
+        if (tid == 0) {  // A~_r[m] = A[r][q'(m)]: q'(p(r)) = ss, q'(p(ss)) = r
+          s_At[pr] = s_Ar[ss];
+          s_At[ps] = s_Ar[r];
+        }
+        dr_part = __reduce_add_sync(FULL, dr_part);
+        ds_part = __reduce_add_sync(FULL, ds_part);
+        if (lane == 0) s_red[warp] = make_int2(dr_part, ds_part);
+        __syncthreads();  // d, the new B'_r, A~_r, the partial sums
+        int dr = 0, ds = 0;
+        for (int w = 0; w < W; ++w) {
+          const int2 v = s_red[w];
+          dr += v.x;
+          ds += v.y;
+        }
+        dR = dr;
+        int8_t *t = s_Bt;
+        s_Bt = s_Bn;
+        s_Bn = t;
+        if (tid == 0) {  // read again only after the next pass's barrier
+          s_d[r] = dr;
+          s_d[ss] = ds;
+          s_p[r] = ps;
+          s_p[ss] = pr;
+          s_q[ps] = r;
+          s_q[pr] = ss;
+        }
+      }
+    }
+    if (s_cur >= N) {  // the row is done: the next row of the cyclic order
+      if (++r >= N - 1) r = 0;
+      s_cur = r + 1;
+      new_row = true;
+    }
+    // ---- block end: hand over below hot_lo, in Delta mode below g.hyb_lo ----
+    if (blk_it >= kHybBlock) {
+      if ((float)blk_acc < g.hyb_lo * (float)blk_it) {
+        mode = 0;
+        handover = true;
+      } else if ((float)blk_acc < hot_lo * (float)blk_it) {
+        handover = true;
+      }
+      blk_it = blk_acc = 0;
+      if (handover) break;
+    }
+  }
+
+  // ---- state back to global memory; B' and Delta are rebuilt by the host's kernels ----
+  cp_async_wait_all();
+  __syncthreads();
+  for (int i = tid; i < N; i += nthreads) {
+    g.p[i] = s_p[i];
+    g.d[i] = s_d[i];
+  }
+  if (tid == 0) {
+    ChainStatus *st = g.st;
+    st->it = it;
+    st->accepts += n_acc;
+    st->cost += d_cost;
+    st->near_ties += n_near;
+    st->exact_evals += n_exact;
+    st->windows += n_pass;
+    st->direct_iters += it - it_start;
+    st->direct_accepts += n_acc;
+    st->hot_iters += it - it_start;
+    st->mode = mode;
+    st->need_rebuild = 1;
+    st->need_bprime = 1;
+    if (handover) st->hot_off = 1;
+    if (err) st->error = err;
+  }
+}
+
+// B'[x][y] = B[p(x)][p(y)] (Eq. 3) from the constant B and the current p, if
+// the hot-phase kernel left B' in global memory stale (grid: ceil(S / blockDim)
+// x N; the padding columns are zero).
+__global__ void hot_bprime_kernel(ChainDev g, const int8_t *__restrict__ B8) {
+  if (!g.st->need_bprime) return;
+  const int N = g.N, S = g.S;
+  const int x = blockIdx.y, y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= S) return;
+  g.Bp[(size_t)x * S + y] = y < N ? B8[(size_t)g.p[x] * S + g.p[y]] : (int8_t)0;
+}
+
+// B as int8 rows of stride S (zero padding), for the hot-phase kernel
+// (grid: ceil(S / blockDim) x N; the entries have been checked to fit int8).
+__global__ void hot_pack_b_kernel(const int *B32, int N, int S, int8_t *B8) {
+  const int x = blockIdx.y, y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= S) return;
+  B8[(size_t)x * S + y] = y < N ? (int8_t)B32[(size_t)x * N + y] : (int8_t)0;
+}
+
+}  // namespace qapsa

@@ -1263,10 +1263,10 @@ __global__ void __launch_bounds__(BOUND, 1)
     sa_tier1_kernel(ChainDev g, unsigned long long it_end) {
   extern __shared__ __align__(16) unsigned char smem[];
   if constexpr (BOUND > kT1SmallThreads) {  // 96 registers a thread: tiles in TMEM;
-                                            // long rows: 4 lanes per proposal
+                                            // long rows: 2 lanes per proposal
     __shared__ unsigned s_tmem;
     const unsigned tb = tile_tmem_acquire(&s_tmem, 4 * kT1R);
-    t1_run_chain<kT1R, true, 4>(g, it_end, smem, tb);
+    t1_run_chain<kT1R, true, 2>(g, it_end, smem, tb);
     tile_tmem_release(&s_tmem);
   } else {
     t1_run_chain<kT1R, false, 1>(g, it_end, smem, 0u);

@@ -907,7 +907,10 @@ __global__ void rebuild_delta_kernel(ChainDev g) {
 }
 
 // Delta in global memory is current again (after rebuild_delta_kernel).
-__global__ void clear_rebuild_kernel(ChainStatus *st) { st->need_rebuild = 0; }
+__global__ void clear_rebuild_kernel(ChainStatus *st) {
+  st->need_rebuild = 0;
+  st->need_bprime = 0;
+}
 
 __global__ void __launch_bounds__(kT2Threads, 1)
     sa_tier2_kernel(ChainDev g, unsigned long long it_end) {

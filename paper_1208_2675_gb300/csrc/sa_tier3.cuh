@@ -6,9 +6,13 @@
 // 2.1), and N beyond a cluster's on-chip memory.
 //
 // Where the data lives during a run:
-//   Delta   M int32 in pair order (packed upper triangle) in global memory;
-//           CTA g owns the pair indices [g M / G, (g + 1) M / G) for the O(1)
-//           update;
+//   Delta   M int32 in pair order (packed upper triangle) in global memory,
+//           twice: every accepted swap reads one copy and writes the other,
+//           so a CTA still scanning a window after a grid barrier never sees
+//           cells another CTA has already moved on to the next swap (the
+//           copies change roles at each barrier; at the end of a launch the
+//           current copy goes back to the first one).  CTA g owns the pair
+//           indices [g M / G, (g + 1) M / G) for the O(1) update;
 //   A, A^T, B, B^T  static int32 rows of stride SA (a multiple of 4) in global
 //           memory (A^T, B^T only for general instances), read with int4 loads
 //           in the rows-r,s recompute and staged into shared memory by TMA bulk
@@ -59,7 +63,8 @@ struct T3Dev {
   int G;                 // CTAs of the grid
   const int *A, *AT, *B, *BT;  // N x SA each (AT == A and BT == B if !general)
   const int *Adiag, *Bdiag;    // N each
-  int *delta;            // M, pair order
+  int *delta;            // M, pair order: the state between launches
+  int *delta2;           // M: the second copy, used during a launch
   int *p;                // N
   int *dR, *dC;          // N each: R_vv = <A_v, B'_v>, C_vv = <A_.v, B'_.v>
   ChainStatus *st;
@@ -257,6 +262,7 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
   int mb = (int)(it % (unsigned long long)M);
   int K = min(kT3Kmin * 2, M);
   unsigned wi = 0;
+  int *Dc = g.delta, *Dn = g.delta2;  // read / written by the current swap
   ChainStatus *nlog = (gb == 0 && tid == 0) ? g.st : nullptr;
   __syncthreads();
 
@@ -290,7 +296,7 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
           if (m >= M) m -= M;
         }
         if (partitioned && (m < lo || m >= hi)) continue;
-        dv[w] = __ldcg(g.delta + m);
+        dv[w] = __ldcg(Dc + m);
         live |= 1u << w;
       }
       if (!live) continue;
@@ -357,7 +363,7 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
       m = mb + j;
       if (m >= M) m -= M;
     }
-    const int dlt = __ldcg(g.delta + m);
+    const int dlt = __ldcg(Dc + m);
     if (code & 1u) {  // undecided by the binary32 pre-test: binary64, the same everywhere
       unsigned long long nt = 0;
       const int dec = exact_accept(g.seed, g.stream, g.T0, g.P, dlt, it + (unsigned)j, &nt,
@@ -477,7 +483,7 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int mm = base + i * kT3Threads;
-          dl[i] = mm < hi ? __ldcg(g.delta + mm) : 0;
+          dl[i] = mm < hi ? __ldcg(Dc + mm) : 0;
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -486,13 +492,13 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
           while (mm >= t3_row_start(N, u + 1)) ++u;  // rows of this thread's cells ascend
           const int v = mm - t3_row_start(N, u) + u + 1;
           if (u == r || u == s || v == r || v == s) {
-            if (u == r && v == s) __stcg(g.delta + mm, -dlt);
+            if (u == r && v == s) __stcg(Dn + mm, -dlt);  // the rest: rows r,s below
             continue;
           }
           int d = dl[i];
           d += (s_a[u] - s_a[v]) * (s_b[v] - s_b[u]);
           d += (s_c[u] - s_c[v]) * (s_e[v] - s_e[u]);  // symmetric: c = a, e = b
-          __stcg(g.delta + mm, d);
+          __stcg(Dn + mm, d);
         }
       }
     }
@@ -585,7 +591,7 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
             val = 2 * (Rxy + Ryx - s_dR[x] - s_dR[v]) + 4 * Ax[v] * Bx[v];
           }
           const int uu = min(x, v), ww = max(x, v);
-          __stcg(g.delta + t3_row_start(N, uu) + (ww - uu - 1), val);
+          __stcg(Dn + t3_row_start(N, uu) + (ww - uu - 1), val);
         }
       }
     }
@@ -593,7 +599,15 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
       err = kT3ErrTimeout;
       break;
     }
+    int *const t = Dc;  // every cell of Dn has been written: it becomes current
+    Dc = Dn;
+    Dn = t;
   }
+
+  // ---- the current copy of this CTA's cells back into g.delta (no CTA reads
+  //      g.delta while it is the other copy; all CTAs swapped equally often) ----
+  if (Dc != g.delta && !err)
+    for (int mm = lo + tid; mm < hi; mm += kT3Threads) __stcg(g.delta + mm, __ldcg(Dc + mm));
 
   // ---- state back to global memory (every CTA holds the same copy) ----
   if (gb == 0) {

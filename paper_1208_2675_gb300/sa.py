@@ -45,7 +45,8 @@ class qap_sa_info(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("total_iters", ctypes.c_uint64),
                 ("smem_bytes", ctypes.c_uint64), ("direct_iters", ctypes.c_uint64),
                 ("direct_accepts", ctypes.c_uint64), ("warp_iters", ctypes.c_uint64),
-                ("ctas", ctypes.c_int32), ("threads", ctypes.c_int32)]
+                ("ctas", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("hot_iters", ctypes.c_uint64)]
 
 
 class qap_peaks(ctypes.Structure):

@@ -261,12 +261,14 @@ def test_full_size_single_chain_n100(N, I):
 
 
 def test_n256_workload_prefix_matches_oracle():
-    """N = 256 under the I = 1e9 schedule: the first 1e5 iterations (the
-    high-acceptance start, about 2e4 accepted swaps) against the oracle."""
+    """N = 256 under the I = 1e9 schedule: the first 3e5 iterations (the
+    high-acceptance start, where the 640-thread kernel's warp-only mode carries
+    the chain) against the oracle, in three launches."""
     A, B, p0 = instances.taixxa_like(256, 1)
     gs, os_, gd, od, _, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=10 ** 9, seed=1,
-                                     oracle_iters=100000)
-    assert os_["accepts"] > 10000
+                                     oracle_iters=300000, splits=[100000, 100000, 100000])
+    assert os_["accepts"] > 50000
+    assert gs["info"]["warp_iters"] > 100000
     assert_same(gs, os_, gd, od)
 
 
@@ -353,8 +355,8 @@ def test_warp_only_direct_mode_gives_the_same_trajectory(N, warp_rate, monkeypat
     """One warp evaluating proposals and applying swaps alone (windows of 32 to
     128, no block barrier) against the oracle; warp_rate 1e-9: whenever the
     chain is in direct mode, 0: never.  Runs split across launches.  The sizes
-    cover one, two and four lanes per proposal and the 256- and 640-thread
-    kernels."""
+    cover the 256-thread kernel (one lane per proposal) and the 640-thread one
+    (two lanes per proposal)."""
     monkeypatch.setenv("QAPSA_HYBRID_RATE", "5e-4")
     monkeypatch.setenv("QAPSA_WARP_RATE", warp_rate)
     A, B, p0 = instances.taixxa_like(N, 43)
@@ -422,3 +424,52 @@ def test_n1024_grid_direct_then_delta_mode_matches_oracle(monkeypatch):
     info = g.info()
     assert info["tier"] == 2 and 16384 <= info["direct_iters"] < I
     assert_same(gs, os_, gd, od)
+
+
+@pytest.mark.parametrize("N,hot,rate,warps,I,iters,splits", [
+    (300, "1", None, None, 300000, 300000, [100000, 200000]),
+    (300, "0", None, None, 300000, 300000, [100000, 200000]),
+    (300, "1", "0.1", "1", 300000, 300000, [100000, 200000]),
+    (300, "1", "0.1", "16", 300000, 300000, [100000, 200000]),
+    (300, "1", "1e-9", "5", 300000, 300000, [1, 149999, 150000]),
+    (1024, "1", None, None, 2 * 10 ** 9, 4000, [1500, 2500]),
+    (0, "1", None, "12", 10 ** 9, 2000, [700, 1300]),
+])
+def test_cluster_hot_phase_kernel_gives_the_same_trajectory(N, hot, rate, warps, I, iters,
+                                                            splits, monkeypatch):
+    """The hot-phase kernel of the cluster tier (one SM, rows of A and B' in L2
+    staged by cp.async) forced on and off, on 1 to 16 warps; state and Delta
+    against the oracle.  N = 300 under a schedule of 3e5 iterations, whose
+    blocks of 16384 iterations accept 0.17, 0.062, 0.015, 0.0063, ... of their
+    proposals: at the default rate 0.01 the kernel hands over after four
+    blocks (Delta rebuilt, the cluster kernel in direct mode), at 0.1 after two;
+    at 1e-9 it keeps the chain until the acceptance falls below the cluster
+    tier's switch to Delta mode (2e-3, about the seventh block) and hands over
+    in Delta mode.  N = 1024 (grid instance) and the largest cluster size
+    (N = 0 here) under their long schedules: the hot kernel all along."""
+    monkeypatch.setenv("QAPSA_HOT", hot)
+    if rate:
+        monkeypatch.setenv("QAPSA_HOT_RATE", rate)
+    if warps:
+        monkeypatch.setenv("QAPSA_HOT_WARPS", warps)
+    if N == 1024:
+        A, B, p0 = instances.grid_instance(32, 1)
+    else:
+        A, B, p0 = instances.taixxa_like(N or sa.qap_sa_max_n_tier(2), 35)
+    gs, os_, gd, od, g, _ = run_both(A, B, p0, t0=0.5, tf=1e-3, I=I, seed=3, stream=1,
+                                     oracle_iters=iters, splits=splits)
+    info = g.info()
+    assert info["tier"] == 2
+    assert os_["accepts"] > 200
+    assert_same(gs, os_, gd, od)
+    blk, pas = 16384, 64  # a block ends with the pass that reaches 16384 iterations
+    if hot == "0":
+        assert info["hot_iters"] == 0
+    elif N != 300:
+        assert info["hot_iters"] == iters
+    elif rate is None:
+        assert 4 * blk <= info["hot_iters"] < 4 * (blk + pas)
+    elif rate == "0.1":
+        assert 2 * blk <= info["hot_iters"] < 2 * (blk + pas)
+    else:
+        assert 5 * blk < info["hot_iters"] < iters

@@ -158,3 +158,20 @@ def test_general_size_limit_and_batch_refusal():
     with pytest.raises(sa.QapError) as e:
         sa.qap_batch_create([dict(A=A, B=B, p0=p0, t0=0.5, tf=1e-3, total_iters=100)])
     assert e.value.status == sa.QAP_E_UNSUPPORTED
+
+
+def test_many_ctas_on_a_small_problem_over_a_long_run(monkeypatch):
+    """76 CTAs on N = 12 (66 cells, most CTAs own none or one) over 2e7
+    iterations: after the grid barrier of an accepted swap some CTAs scan the
+    next short window while others have found its swap and update their cells.
+    The swap reads one copy of Delta and writes the other, so the slow CTAs
+    still read the cells they must; with one copy they would see cells of the
+    next swap, take another decision and never meet the others at the barrier."""
+    monkeypatch.setenv("QAPSA_TIER", "3")
+    monkeypatch.setenv("QAPSA_T3_GRID", "76")
+    A, B, p0 = instances.taixxa_like(12, 1)
+    I = 2 * 10 ** 7
+    g, o = run_both(A, B, p0, I=I, seed=1, stream=1, splits=[I // 2, I - I // 2])
+    assert g.info()["ctas"] == 76
+    st = assert_same(g, o)
+    assert st["accepts"] > 1000
