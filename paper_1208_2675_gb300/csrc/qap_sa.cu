@@ -222,7 +222,6 @@ struct qap_sa {
   int hot = 0;
   int8_t *B8 = nullptr;  // B as int8 rows of stride S (the hot-phase kernel's)
   int hot_warps = 0;
-  int hot_depth = 0;
   int hot_smem = 0;
   float hot_lo = 0.0f;
   // tier 3 (a persistent grid, Delta in global memory)
@@ -906,16 +905,13 @@ int create_common(const int32_t *A32, const int32_t *B32, int32_t N,
       const char *eh = getenv("QAPSA_HOT");
       const char *el = getenv("QAPSA_HOT_RATE");
       const char *ewp = getenv("QAPSA_HOT_WARPS");
-      const char *edp = getenv("QAPSA_HOT_DEPTH");
       h->hot_lo = el ? (float)atof(el) : kHotRateDefault;
-      int W = ewp ? atoi(ewp) : kHotWarpsDefault;
-      W = W < 1 ? 1 : (W > kHotMaxWarps ? kHotMaxWarps : W);
-      int D = edp ? atoi(edp) : kHotDepthDefault;
-      D = D < 1 ? 1 : (D > 4 ? 4 : D);
-      while (W > 1 && hot_layout(N, S, W, D).bytes > device_smem_optin()) --W;
+      const int want = ewp ? atoi(ewp) : kHotWarpsDefault;
+      int W = 1;  // a power of two
+      while (2 * W <= want && 2 * W <= kHotMaxWarps) W *= 2;
+      while (W > 1 && hot_layout(N, S, W).bytes > device_smem_optin()) W /= 2;
       h->hot_warps = W;
-      h->hot_depth = D;
-      h->hot_smem = hot_layout(N, S, W, D).bytes;
+      h->hot_smem = hot_layout(N, S, W).bytes;
       h->hot = (eh ? atoi(eh) != 0 : true) && h->hot_lo > 0.0f && g.hyb_lo > 0.0f &&
                h->hot_smem <= device_smem_optin();
       if (h->hot) {
@@ -1055,8 +1051,7 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
         // the hot phase first (it returns at once after it has handed the
         // chain over); it leaves B' and Delta in global memory to be rebuilt
         sa_hot_kernel<<<1, 32 * h->hot_warps, h->hot_smem, h->stream>>>(h->dev, h->B8, stop,
-                                                                          h->hot_lo,
-                                                                          h->hot_depth);
+                                                                          h->hot_lo);
         hot_bprime_kernel<<<dim3((h->S + 255) / 256, h->N), 256, 0, h->stream>>>(h->dev, h->B8);
         rebuild_delta_kernel<<<dim3((h->N + 127) / 128, h->N), 128, 0, h->stream>>>(h->dev);
         clear_rebuild_kernel<<<1, 1, 0, h->stream>>>(h->st);

@@ -16,18 +16,18 @@
 // order run along row r (s = r+1 .. N-1) before moving to row r+1, so A~_r and
 // B'_r serve a whole row; each proposal needs rows A_s and B_p(s) of the
 // constant matrices, which the kernel streams from global memory (L2) with
-// cp.async into a ring of shared-memory slots a few passes ahead.  A staged row stays
+// cp.async into a ring of shared-memory slots a pass ahead.  A staged row stays
 // valid across accepted swaps of its row sweep: an accepted (r, s*) changes p
 // only at r and s*, and the rows still to come have s > s*.
 //
 //   pass    group g (eight lanes; four groups a warp) takes proposal s of the
 //           window [s_cur, s_cur + K) with s = g mod P (P = 4 W): its rows
-//           are in slot s mod (D+1)P, and it keeps the copies of s + P .. s + DP
-//           issued (D passes ahead, so that a row is asked for a few passes
-//           before it is read), and draws the Philox word of its proposal and
-//           forms the binary32 interval for Eq. (2).  The first accepted (or
-//           undecided) proposal in sequential order: redux.min per warp, one
-//           CTA barrier.
+//           are in slot s mod 2P, and it keeps the copies of s + P issued.
+//           The Philox word of the proposal and its binary32 interval for
+//           Eq. (2) come from a table that a warp with no proposal in the pass
+//           fills for the iterations after it (the group draws them itself when
+//           the table has no entry).  The first accepted (or undecided)
+//           proposal in sequential order: redux.min per warp, one CTA barrier.
 //   accept  (r, s*), from the staged rows of s*: d_k += (A_rk - A_s*k)(B'_s*k
 //           - B'_rk) off r, s*; the new B'_r (a gather of B_p(s*) by the new p)
 //           into the second buffer; d_r, d_s* by a reduction; two entries of
@@ -48,11 +48,9 @@ namespace qapsa {
 
 constexpr int kHotPPW = 4;        // proposals (groups) per warp
 constexpr int kHotLPP = 8;        // lanes per proposal
-constexpr int kHotMaxWarps = 16;
+constexpr int kHotMaxWarps = 16;  // a power of two, as W must be
 constexpr int kHotWarpsDefault = 8;
-constexpr int kHotDepthDefault = 2;  // passes the row copies run ahead
-// Acceptance rate below which the hot-phase kernel hands a chain over to the
-// cluster kernel (whose own switch to Delta mode is at g.hyb_lo).
+constexpr int kHotTab = 256;      // entries of the table of Eq. (2) intervals
 // From whole-piece timings of the N = 1024 schedule: per 1e8 iterations the
 // hot kernel takes 17.6 s against the cluster kernel's 30.9 s at acceptance
 // 0.05 and 11.1 s against 13.7 s at 0.019; the lines cross near 0.013.
@@ -61,12 +59,12 @@ constexpr float kHotRateDefault = 0.012f;
 struct HotLayout {
   int off_p, off_q, off_d;                      // int32 vectors
   int off_Ar, off_At, off_Bt0, off_Bt1, off_Br; // int8 rows of S bytes
-  int off_key, off_slot, off_red, off_ctl;
-  int off_ring;                                 // (D+1)P slots of (A_s, B_p(s))
+  int off_key, off_slot, off_red, off_ctl, off_tab;
+  int off_ring;                                 // 2P slots of (A_s, B_p(s))
   int bytes;
 };
 
-__host__ __device__ inline HotLayout hot_layout(int N, int S, int W, int D) {
+__host__ __device__ inline HotLayout hot_layout(int N, int S, int W) {
   HotLayout L;
   const int NP = t1_vec_len(N);
   const int P = kHotPPW * W;
@@ -84,7 +82,8 @@ __host__ __device__ inline HotLayout hot_layout(int N, int S, int W, int D) {
   L.off_red = o;  o += 8 * kHotMaxWarps;
   L.off_ctl = o;  o += 16;
   o = align16(o);
-  L.off_ring = o; o += (D + 1) * P * 2 * S;
+  L.off_tab = o;  o += 16 * kHotTab;
+  L.off_ring = o; o += 2 * P * 2 * S;
   L.bytes = o;
   return L;
 }
@@ -104,14 +103,20 @@ __device__ __forceinline__ void cp_async_wait_prior() {
   asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
 
+// The binary32 interval of Eq. (2) for the proposal made at iteration itc.
+__device__ __forceinline__ float2 hot_interval(const ChainDev &g, unsigned long long itc) {
+  const uint4 x = rng_block(g.seed, g.stream, itc >> 2);
+  const float Tc = g.T0f * exp2f(u64_to_f32(itc) * g.log2a_f);
+  return accept_interval(g.mrel, Tc, word_of(x, (int)(itc & 3u)));
+}
+
 // g: the chain (A with rows of stride S; g.Bp, g.delta not used); B8: the
 // constant B with rows of stride S; hot_lo: the acceptance rate below which
-// the kernel hands the chain over; D >= 1: passes the row copies run ahead.
-// One CTA of 32 W threads (W <= kHotMaxWarps) with hot_layout(N, S, W, D).bytes
-// of dynamic shared memory.
+// the kernel hands the chain over.  One CTA of 32 W threads, W a power of two
+// up to kHotMaxWarps, with hot_layout(N, S, W).bytes of dynamic shared memory.
 __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
     sa_hot_kernel(ChainDev g, const int8_t *__restrict__ B8, unsigned long long it_end,
-                  float hot_lo, int D) {
+                  float hot_lo) {
   extern __shared__ __align__(16) unsigned char smem[];
   {
     const ChainStatus *st = g.st;
@@ -123,9 +128,9 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
   const int N = g.N, S = g.S, M = g.M, NC = S >> 4;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthreads = blockDim.x, W = nthreads >> 5;
-  const int P = kHotPPW * W;  // proposals a pass covers at most
-  const int R = (D + 1) * P;  // ring slots
-  const HotLayout L = hot_layout(N, S, W, D);
+  const int P = kHotPPW * W;    // proposals a pass covers at most (a power of two)
+  const int R = 2 * P;          // ring slots
+  const HotLayout L = hot_layout(N, S, W);
   int *s_p = reinterpret_cast<int *>(smem + L.off_p);
   int *s_q = reinterpret_cast<int *>(smem + L.off_q);
   int *s_d = reinterpret_cast<int *>(smem + L.off_d);
@@ -138,6 +143,9 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
   int2 *s_slot = reinterpret_cast<int2 *>(smem + L.off_slot);
   int2 *s_red = reinterpret_cast<int2 *>(smem + L.off_red);
   int *s_dec = reinterpret_cast<int *>(smem + L.off_ctl);
+  // interval of the proposal at iteration i in entry i mod kHotTab: (lo, hi,
+  // the low 32 bits of i, unused)
+  float4 *s_tab = reinterpret_cast<float4 *>(smem + L.off_tab);
   int8_t *s_ring = reinterpret_cast<int8_t *>(smem + L.off_ring);
   const int8_t *gA = g.A;
 
@@ -147,6 +155,8 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
     s_d[i] = i < N ? g.d[i] : 0;
   }
   for (int k = N + tid; k < S; k += nthreads) s_Bn[k] = 0;  // padding of the second buffer
+  for (int i = tid; i < kHotTab; i += nthreads)
+    s_tab[i] = make_float4(0.0f, 0.0f, __uint_as_float(~(unsigned)i), 0.0f);  // no entry
   __syncthreads();
   for (int i = tid; i < N; i += nthreads) s_q[s_p[i]] = i;
 
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
 
   // copies of the rows of proposal s into its slot (by the eight lanes of its group)
   auto issue = [&](int s) {
-    int8_t *dst = s_ring + (size_t)(s % R) * (2 * S);
+    int8_t *dst = s_ring + (size_t)(s & (R - 1)) * (2 * S);
     const int8_t *srcA = gA + (size_t)s * S;
     const int8_t *srcB = B8 + (size_t)s_p[s] * S;
     for (int c = sub; c < NC; c += kHotLPP) {
@@ -188,10 +198,11 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
         if (c < NC) cp_async16(s_Ar + 16 * c, ra + 16 * c);
         else cp_async16(s_Br + 16 * (c - NC), rb + 16 * (c - NC));
       }
-      // this group's first proposal of the row and the D after it
-      const int s0 = s_cur + ((G - s_cur % P) % P + P) % P;
-      for (nx = s0; nx <= s0 + D * P && nx < N; nx += P) issue(nx);
-      nx = s0 + (D + 1) * P;
+      // this group's first proposal of the row and the one a pass later
+      const int s0 = s_cur + ((G - s_cur) & (P - 1));
+      if (s0 < N) issue(s0);
+      if (s0 + P < N) issue(s0 + P);
+      nx = s0 + 2 * P;
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
@@ -205,49 +216,88 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
     }
     // ================= one pass: proposals s_cur .. s_cur + plen - 1 =================
     const int plen = (int)min((unsigned long long)min(K, N - s_cur), it_end - it);
-    const int sg = s_cur + ((G - s_cur % P) % P + P) % P;  // this group's proposal
-    const int j = sg - s_cur;                                // its offset in the pass
+    const int j = (G - s_cur) & (P - 1);  // this group's offset in the pass
+    const int sg = s_cur + j;             // and its proposal
     const bool live = j < plen;
-    // keep the group's next D proposals staged
-    while (nx <= sg + D * P && nx < N) {
+    // keep the group's next proposal staged a pass ahead
+    while (nx <= sg + P && nx < N) {
       issue(nx);
       nx += P;
     }
     cp_async_commit();
-    // Eq. (2) interval of this proposal, and d_s
     float2 bnd = make_float2(0.0f, 0.0f);
     int dsg = 0;
-    if (live && sub == 0) {
-      const unsigned long long itc = it + (unsigned)j;
-      const uint4 x = rng_block(g.seed, g.stream, itc >> 2);
-      const float Tc = g.T0f * exp2f(u64_to_f32(itc) * g.log2a_f);
-      bnd = accept_interval(g.mrel, Tc, word_of(x, (int)(itc & 3u)));
-      dsg = s_d[sg];
+    if (__any_sync(FULL, live)) {
+      // Eq. (2) interval of this proposal (from the table when an idle warp
+      // has drawn it) and d_s while the copies complete
+      if (live && sub == 0) {
+        const unsigned long long itc = it + (unsigned)j;
+        const float4 e = s_tab[itc & (kHotTab - 1)];
+        if (__float_as_uint(e.z) == (unsigned)itc) {
+          bnd = make_float2(e.x, e.y);
+        } else {
+          bnd = hot_interval(g, itc);
+          s_tab[itc & (kHotTab - 1)] = make_float4(bnd.x, bnd.y, __uint_as_float((unsigned)itc), 0.0f);
+        }
+        dsg = s_d[sg];
+      }
+    } else {
+      // an idle warp: the first idle one draws the intervals of the 128
+      // iterations after the pass (the next passes' windows lie in them)
+      int first_idle = -1;
+      for (int w = 0; w < W && first_idle < 0; ++w) {
+        const int jmin = (4 * w - s_cur) & (P - 1);  // offsets of its groups: jmin .. jmin+3 mod P
+        bool any_live = false;
+#pragma unroll
+        for (int gg = 0; gg < kHotPPW; ++gg) any_live |= ((jmin + gg) & (P - 1)) < plen;
+        if (!any_live) first_idle = w;
+      }
+      if (warp == first_idle) {
+        const unsigned long long a = it + (unsigned)plen;
+        const unsigned long long q = (a >> 2) + (unsigned)lane;
+        const uint4 x = rng_block(g.seed, g.stream, q);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const unsigned long long itc = (q << 2) + (unsigned)w;
+          if (itc < a) continue;  // inside this pass: its groups draw them
+          const float Tc = g.T0f * exp2f(u64_to_f32(itc) * g.log2a_f);
+          const float2 b = accept_interval(g.mrel, Tc, word_of(x, w));
+          s_tab[itc & (kHotTab - 1)] = make_float4(b.x, b.y, __uint_as_float((unsigned)itc), 0.0f);
+        }
+      }
     }
     cp_async_wait_prior();  // the copies of proposal sg (issued a pass or more ago)
     __syncwarp();
     int g1 = 0, g2 = 0;
     if (live) {
-      const int8_t *slot = s_ring + (size_t)(sg % R) * (2 * S);
+      const int8_t *slot = s_ring + (size_t)(sg & (R - 1)) * (2 * S);
       const int4 *As4 = reinterpret_cast<const int4 *>(slot);
       const int4 *Bs4 = reinterpret_cast<const int4 *>(slot + S);
       const int4 *At4 = reinterpret_cast<const int4 *>(s_At);
       const int4 *Bt4 = reinterpret_cast<const int4 *>(s_Bt);
+      int a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
 #pragma unroll 3
       for (int c = sub; c < NC; c += kHotLPP) {
-        g1 = dot16x(At4[c], Bs4[c], g1);  // <A~_r, B_p(s)> = <A_r, B'_s>
-        g2 = dot16x(As4[c], Bt4[c], g2);  // <A_s, B'_r>
+        const int4 x = At4[c], y = Bs4[c], u = As4[c], v = Bt4[c];
+        a0 = __dp4a(x.x, y.x, a0);  // <A~_r, B_p(s)> = <A_r, B'_s>
+        a1 = __dp4a(x.y, y.y, a1);
+        a2 = __dp4a(x.z, y.z, a2);
+        a3 = __dp4a(x.w, y.w, a3);
+        b0 = __dp4a(u.x, v.x, b0);  // <A_s, B'_r>
+        b1 = __dp4a(u.y, v.y, b1);
+        b2 = __dp4a(u.z, v.z, b2);
+        b3 = __dp4a(u.w, v.w, b3);
       }
+      g1 = (a0 + a1) + (a2 + a3);
+      g2 = (b0 + b1) + (b2 + b3);
     }
+    int gs = g1 + g2;
 #pragma unroll
-    for (int o = 1; o < kHotLPP; o <<= 1) {
-      g1 += __shfl_xor_sync(FULL, g1, o);
-      g2 += __shfl_xor_sync(FULL, g2, o);
-    }
+    for (int o = 1; o < kHotLPP; o <<= 1) gs += __shfl_xor_sync(FULL, gs, o);
     unsigned best = kNone;
     int dv = 0;
     if (live && sub == 0) {
-      dv = 2 * (g1 + g2 - dR - dsg + 2 * (int)s_Ar[sg] * (int)s_Bt[sg]);
+      dv = 2 * (gs - dR - dsg + 2 * (int)s_Ar[sg] * (int)s_Bt[sg]);
       const float df = (float)dv;
       unsigned acc = 0, unc = 0;
       if (dv <= 0 || df < bnd.x) acc = 1u;
@@ -257,7 +307,7 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
     const unsigned wmin = __reduce_min_sync(FULL, best);
     if (best != kNone && best == wmin) s_slot[par * kHotMaxWarps + warp] = make_int2(sg, dv);
     if (lane == 0) s_key[par * kHotMaxWarps + warp] = wmin;
-    __syncthreads();  // keys and slots (and thread 0's d, p, q of the last swap)
+    __syncthreads();  // keys, slots, the table (and thread 0's d, p, q of the last swap)
     const unsigned code =
         __reduce_min_sync(FULL, lane < W ? s_key[par * kHotMaxWarps + lane] : kNone);
     const unsigned pp = par;
@@ -273,7 +323,7 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
       const int jw = (int)(code >> 1);
       const int s_old = s_cur;
       // the winner's warp: its group is (s_old + jw) mod P
-      const int2 sl = s_slot[pp * kHotMaxWarps + ((s_old + jw) % P) / kHotPPW];
+      const int2 sl = s_slot[pp * kHotMaxWarps + ((s_old + jw) & (P - 1)) / kHotPPW];
       const int ss = sl.x, dlt = sl.y;
       bool take = true;
       if (code & 1u) {  // undecided by the binary32 pre-test: binary64
@@ -300,7 +350,7 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
           ++n_acc;
           d_cost += dlt;
         }
-        const int8_t *slot = s_ring + (size_t)(ss % R) * (2 * S);
+        const int8_t *slot = s_ring + (size_t)(ss & (R - 1)) * (2 * S);
         const int8_t *As = slot, *Bps = slot + S;  // A_ss and B_p(ss)
         const int pr = s_p[r], ps = s_p[ss];
         int dr_part = 0, ds_part = 0;
