@@ -51,10 +51,12 @@ constexpr int kHotLPP = 8;        // lanes per proposal
 constexpr int kHotMaxWarps = 16;  // a power of two, as W must be
 constexpr int kHotWarpsDefault = 8;
 constexpr int kHotTab = 256;      // entries of the table of Eq. (2) intervals
-// From whole-piece timings of the N = 1024 schedule: per 1e8 iterations the
-// hot kernel takes 17.6 s against the cluster kernel's 30.9 s at acceptance
-// 0.05 and 11.1 s against 13.7 s at 0.019; the lines cross near 0.013.
-constexpr float kHotRateDefault = 0.012f;
+// From whole-piece timings of the N = 1024 schedule, seconds per 1e8
+// iterations at acceptance 0.019 / 0.012 / 0.007: this kernel 8.3 / 7.3 /
+// 6.7; the cluster kernel maintaining Delta 18.8 / 11.8 / 7.2 (about 10 us per
+// accepted swap), in its direct mode 13.7 / - / 5.7.  The kernel keeps the
+// chain down to 0.009, the cluster's direct mode takes it from there.
+constexpr float kHotRateDefault = 0.009f;
 
 struct HotLayout {
   int off_p, off_q, off_d;                      // int32 vectors
