@@ -193,15 +193,15 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------- #
-# roofline of the SA kernel (the method's algorithmic bytes)
+# roofline of the dominant kernel
 # --------------------------------------------------------------------------- #
-def roofline(wl, info, accepts, t_kernel, peaks, sms_held):
-    """Bytes by the method's own count: an iteration reads one Delta cell
-    (4 B); an accepted swap reads and writes every one of the M cells (8 B) and
-    reads A and B' once for rows r,s (2 w B per cell, w = 1 for the int8 rows).
-    Peak: shared memory of the SMs the chain holds, at the measured bytes per
-    clock and SM clock of this GPU.  The kernel moves no DRAM bytes per
-    iteration: its state stays on chip."""
+def delta_method_roofline(wl, info, accepts, t_kernel, peaks, sms_held):
+    """The Delta-matrix method's bytes by its own count: an iteration reads one
+    Delta cell (4 B); an accepted swap reads and writes every one of the M
+    cells (8 B) and reads A and B' once for rows r,s (2 w B per cell, w = 1 for
+    the int8 rows).  Peak: shared memory of the SMs the chain holds, at the
+    measured bytes per clock and SM clock of this GPU.  The kernel moves no
+    DRAM bytes per iteration: its state stays on chip."""
     N, I = wl["N"], info["iterations"]
     M = N * (N - 1) // 2
     w = 1
@@ -209,9 +209,10 @@ def roofline(wl, info, accepts, t_kernel, peaks, sms_held):
     achieved = algo / t_kernel / 1e9
     per_sm = peaks["smem_bytes_per_clk_sm"] * peaks["sm_mhz"] * 1e6 / 1e9
     peak = per_sm * sms_held
-    # what the kernel actually moved: a proposal evaluated directly reads rows
-    # r,s of A and B' (4N), a direct accept moves O(N) (6N), a proposal read
-    # from Delta is 4 B, an accept with Delta maintained is 8M + 2N^2
+    # what the kernels actually moved: a proposal evaluated directly reads rows
+    # of A and B (4N on chip, or 2N from L2 in the hot-phase kernel), a direct
+    # accept moves O(N) (6N), a proposal read from Delta is 4 B, an accept with
+    # Delta maintained is 8M + 2N^2
     d_it, d_acc = info["direct_iters"], info["direct_accepts"]
     moved = d_it * 4 * N + d_acc * 6 * N + (I - d_it) * 4 + (accepts - d_acc) * (8 * M + 2 * N * N)
     nbar = 2  # hardware barriers per accepted swap (CTA or cluster)
@@ -233,6 +234,51 @@ def roofline(wl, info, accepts, t_kernel, peaks, sms_held):
                     "basis": "two hardware barriers per accepted swap at the measured "
                              "barrier latency: the floor a chain of dependent accepts "
                              "cannot go below"},
+    }
+
+
+def roofline(wl, info, accepts, t_kernel, peaks, sms_held, ktimes=None):
+    """The roofline of the kernel that takes most of the device time (CUDA
+    events around every launch, qap_sa_kernel_times).  For the cluster tier's
+    hot-phase kernel (one SM): a proposal streams rows A_s and B_p(s) (int8, 2N
+    bytes) from L2 into shared memory and everything else stays on chip, so
+    the bound is what one SM draws from L2 (measured, qap_peaks_measure
+    l2_gbs_sm); an accepted swap is a dependent chain of two CTA barriers.  For
+    the other kernels: the Delta-matrix method's count (delta_method_roofline),
+    which is also reported beside the hot kernel's for the whole run."""
+    dm = delta_method_roofline(wl, info, accepts, t_kernel, peaks, sms_held)
+    if not ktimes or ktimes["hot"][0] <= ktimes["sa"][0]:
+        if ktimes:
+            dm["kernel"] = "sa_tier1_kernel" if sms_held == 1 else "sa_tier2_kernel"
+            dm["share_of_device_time"] = ktimes["sa"][0] / max(1e-12, sum(v[0] for v in ktimes.values()))
+        return dm
+    N = wl["N"]
+    t_hot, n_hot = ktimes["hot"]
+    hot_it, hot_acc = info["hot_iters"], info["hot_accepts"]
+    algo = hot_it * 2 * N
+    achieved = algo / t_hot / 1e9
+    peak = peaks["l2_gbs_sm"]
+    per_acc_ns = t_hot / max(hot_acc, 1) * 1e9
+    floor_ns = 2 * peaks["cta_barrier_ns"]
+    total = sum(v[0] for v in ktimes.values())
+    return {
+        "bound": "l2", "kernel": "sa_hot_kernel", "achieved": achieved, "peak": peak,
+        "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+        "algorithmic_bytes_per_launch": algo / max(n_hot, 1), "launches": n_hot,
+        "avg_launch_s": t_hot / max(n_hot, 1),
+        "bytes_basis": "2N per proposal evaluated: rows A_s and B_p(s), int8, streamed "
+                       "from L2 (hot_iters x 2N over the kernel's event-timed seconds)",
+        "peak_basis": f"measured ld.global.cg from L2 by one CTA of 1024 threads: "
+                      f"{peak:.1f} GB/s (qap_peaks_measure l2_gbs_sm)",
+        "share_of_device_time": t_hot / max(total, 1e-12),
+        "kernel_seconds": {k: v[0] for k, v in ktimes.items()},
+        "kernel_launches": {k: v[1] for k, v in ktimes.items()},
+        "hot_iters": hot_it, "hot_accepts": hot_acc,
+        "latency": {"ns_per_accept": per_acc_ns, "floor_ns_per_accept": floor_ns,
+                    "frac_of_floor": floor_ns / per_acc_ns,
+                    "basis": "two CTA barriers per accepted swap at the measured barrier "
+                             "latency (the pass that finds it, the update)"},
+        "delta_method": dm,
     }
 
 
@@ -288,6 +334,7 @@ def run_chain_workload(args, wl, rank, world, dev, dist, peaks, timed=True):
     ev_set[0].record(stream)
     h = sa.Chain.from_device(At, Bt, pt, stream=stream.cuda_stream, **kw)
     ev_set[1].record(stream)
+    h.set_timing(True)
     for k, n in enumerate(pieces(I, K)):
         ev[k][0].record(stream)
         h.run_async(n)
@@ -298,6 +345,7 @@ def run_chain_workload(args, wl, rank, world, dev, dist, peaks, timed=True):
     clk = clocks.stop() if clocks else None
     h.sync()
     info = h.info()
+    ktimes = h.kernel_times()
     h.close()
     t_setup = ev_set[0].elapsed_time(ev_set[1]) / 1e3
     t_pieces = [e[0].elapsed_time(e[1]) / 1e3 for e in ev]
@@ -305,12 +353,19 @@ def run_chain_workload(args, wl, rank, world, dev, dist, peaks, timed=True):
     t_dev_max = replicas.max_over_ranks(t_dev, dist, dev)
     t_e2e_max = replicas.max_over_ranks(t1 - t0, dist, dev)
     p_fin, cost_fin, acc_fin = results[-1]
+    # kernels launched: the set-up (classify, pack, B', Gram, Delta_0, and B as
+    # int8 for the hot kernel), then per launch of 2^26 iterations one SA
+    # kernel (one SM), or on the cluster tier the hot kernel with its B' and
+    # Delta rebuild (4) and two cluster launches each with a Delta rebuild (6)
     chunk = int(os.environ.get("QAPSA_CHUNK_ITERS", str(1 << 26)))
-    per_piece_launches = [-(-n // chunk) * (4 if info["tier"] == 2 else 1) for n in pieces(I, K)]
+    hot = ktimes["hot"][1] > 0
+    per_chunk = (10 if hot else 6) if info["tier"] == 2 else 1
+    setup = 6 if hot else 5
+    per_piece_launches = [-(-n // chunk) * per_chunk for n in pieces(I, K)]
     return {"N": N, "I": I, "t_dev": t_dev_max, "t_e2e": t_e2e_max, "t_setup": t_setup,
-            "t_kernel": sum(t_pieces), "t_pieces": t_pieces, "info": info,
+            "t_kernel": sum(t_pieces), "t_pieces": t_pieces, "info": info, "ktimes": ktimes,
             "accepts": acc_fin, "cost": cost_fin, "clocks": clk,
-            "launches": 4 + sum(per_piece_launches),
+            "launches": setup + sum(per_piece_launches),
             "h2d": 2 * N * N * 4 + 4 * N, "d2h_per_step": 4 * N + 8 + 8}
 
 
@@ -362,7 +417,7 @@ def run_ours(args, rank, world, local_rank, dist):
                             "accept_rate": x["accepts"] / x["I"],
                             "s_per_run": x["t_dev"],
                             "roofline": roofline(WORKLOADS[name], x["info"], x["accepts"],
-                                                 x["t_kernel"], peaks, 1)}
+                                                 x["t_kernel"], peaks, 1, x["ktimes"])}
         extras["batch512"] = batch_fields(rank, world, dev, dist, steps=1, warmup=1)
         if rank == 0:
             extras["serve_sample"] = serve_sweep(SERVE_SAMPLE["count"], SERVE_SAMPLE["rates"],
@@ -372,7 +427,7 @@ def run_ours(args, rank, world, local_rank, dist):
     I, N = wl["I"], wl["N"]
     value = world * I / r["t_dev"]
     acc = r["accepts"]
-    rl = roofline(wl, info, acc, r["t_kernel"], peaks, sms_held)
+    rl = roofline(wl, info, acc, r["t_kernel"], peaks, sms_held, r["ktimes"])
     traffic = PROFILED_TRAFFIC.get(args.workload)
     if traffic:
         rl["traffic"] = traffic["bytes_per_launch"]
@@ -400,7 +455,8 @@ def run_ours(args, rank, world, local_rank, dist):
         "final_cost": r["cost"],
         "delta_cell_updates_per_sec": world * (acc - info["direct_accepts"]) * M / r["t_dev"],
         "direct_proposals_per_sec": world * info["direct_iters"] / r["t_dev"],
-        "modes": {"direct_iters": info["direct_iters"], "direct_accepts": info["direct_accepts"],
+        "modes": {"hot_iters": info["hot_iters"], "hot_accepts": info["hot_accepts"],
+                  "direct_iters": info["direct_iters"], "direct_accepts": info["direct_accepts"],
                   "delta_iters": I - info["direct_iters"],
                   "delta_accepts": acc - info["direct_accepts"], "tier": info["tier"],
                   "sms_held": sms_held},

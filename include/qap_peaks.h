@@ -45,6 +45,8 @@ typedef struct qap_peaks {
   double l2_latency_ns;           /* one dependent ld.global.cg (L2 hit)       */
   double dsmem_latency_ns;        /* one dependent ld.shared::cluster of a peer CTA */
   double smem_latency_ns;         /* one dependent ld.shared                   */
+  double l2_gbs_sm;               /* ld.global.cg of an L2-resident 8 MB buffer by
+                                     one CTA of 1024 threads: what one SM draws  */
 } qap_peaks;
 
 QAP_EXPORT int qap_peaks_measure(qap_peaks *out);

@@ -173,8 +173,29 @@ typedef struct qap_sa_info {
   uint64_t hot_iters;     /* iterations run by the hot-phase kernel of the
                              cluster tier (one SM, rows of A and B' in L2)
                              while the acceptance rate was high            */
+  uint64_t hot_accepts;   /* accepted swaps among them                      */
 } qap_sa_info;
 QAP_EXPORT int qap_sa_get_info(qap_sa *h, qap_sa_info *out);
+
+/* Device time of a handle's kernels, by kind, from CUDA events recorded on
+ * the handle's stream around every launch of qap_sa_run / qap_sa_run_async
+ * while timing is on (off by default; events cost a few microseconds per
+ * launch of 2^26 iterations).  Kinds:                                      */
+#define QAP_KT_HOT 0   /* the cluster tier's hot-phase kernel (one SM)      */
+#define QAP_KT_SA 1    /* the SA kernel of the chain's tier (one SM,
+                          cluster or grid)                                  */
+#define QAP_KT_AUX 2   /* the B' and Delta rebuilds between them            */
+#define QAP_KT_COUNT 3
+/* on != 0 starts timing (and clears what was counted), 0 stops it.
+ * QAP_E_INVAL for h == NULL.                                               */
+QAP_EXPORT int qap_sa_set_timing(qap_sa *h, int on);
+/* After a sync of the handle's stream: seconds[k] and launches[k], k <
+ * QAP_KT_COUNT (caller-owned arrays), the device time and the number of timed
+ * launches of kind k (a rebuild of B' and Delta, two or three small kernels,
+ * counts as one) since timing was switched on or last read; the counts start
+ * again.
+ * QAP_E_INVAL for NULL arguments, QAP_E_CUDA if an event failed.            */
+QAP_EXPORT int qap_sa_kernel_times(qap_sa *h, double *seconds, uint64_t *launches);
 
 /* The current Delta (after a stream sync) as M int32 values in pair order
  * (r < s, row-major): delta_out[m] is the cost change of swapping pair(m).  */

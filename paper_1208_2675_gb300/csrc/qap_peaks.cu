@@ -328,6 +328,16 @@ extern "C" int qap_peaks_measure(qap_peaks *out) {
     PK_CK(cudaGetLastError());
     PK_CK(cudaEventElapsedTime(&ms, e0, e1));
     out->l2_gbs = ms > 0 ? (double)n4 * 16.0 * passes / (ms * 1e-3) / 1e9 : 0.0;
+    // one SM: the first 8 MB of the (L2-resident) buffer, read by one CTA
+    const long long m4 = n4 < (1ll << 19) ? n4 : (1ll << 19);
+    const int passes1 = 4;
+    PK_CK(cudaEventRecord(e0));
+    pk_l2_bw<<<1, 1024>>>(s.buf, m4, passes1, s.sink);
+    PK_CK(cudaEventRecord(e1));
+    PK_CK(cudaEventSynchronize(e1));
+    PK_CK(cudaGetLastError());
+    PK_CK(cudaEventElapsedTime(&ms, e0, e1));
+    out->l2_gbs_sm = ms > 0 ? (double)m4 * 16.0 * passes1 / (ms * 1e-3) / 1e9 : 0.0;
   }
 
   // ---- integer issue rates ----

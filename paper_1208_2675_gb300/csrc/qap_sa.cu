@@ -232,6 +232,13 @@ struct qap_sa {
   unsigned long long *bar3 = nullptr;
   unsigned *keys3 = nullptr;
   T3Dev dev3{};
+  // CUDA-event timing of the launches (qap_sa_set_timing)
+  struct TimedLaunch {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  int timing = 0;
+  std::vector<TimedLaunch> timed;
 };
 
 namespace {
@@ -243,6 +250,29 @@ namespace {
 void dfree(void *p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
 }
+
+// Event pair around the launches of one scope, of kernel kind k, on the
+// handle's stream while timing is on.
+struct LaunchTimer {
+  qap_sa *h;
+  int k;
+  cudaEvent_t a = nullptr, b = nullptr;
+  LaunchTimer(qap_sa *h_, int k_) : h(h_), k(k_) {
+    if (!h->timing) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      if (a) cudaEventDestroy(a);
+      a = b = nullptr;
+      cudaGetLastError();
+      return;
+    }
+    cudaEventRecord(a, h->stream);
+  }
+  ~LaunchTimer() {
+    if (!a) return;
+    cudaEventRecord(b, h->stream);
+    h->timed.push_back({k, a, b});
+  }
+};
 
 void free_handle(qap_sa *h) {
   if (!h) return;
@@ -267,6 +297,10 @@ void free_handle(qap_sa *h) {
   dfree(h->dC3, st);
   dfree(h->bar3, st);
   dfree(h->keys3, st);
+  for (auto &t : h->timed) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
   if (h->own_stream && st) cudaStreamDestroy(st);
   delete h;
 }
@@ -1037,8 +1071,12 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
       void *args[] = {&d3, &e3};
       const void *k = h->general ? (const void *)sa_tier3_kernel<true>
                                  : (const void *)sa_tier3_kernel<false>;
-      cudaError_t el = cudaLaunchCooperativeKernel(k, dim3(h->dev3.G), dim3(kT3Threads), args,
-                                                   (size_t)h->smem_bytes, h->stream);
+      cudaError_t el;
+      {
+        LaunchTimer t(h, QAP_KT_SA);
+        el = cudaLaunchCooperativeKernel(k, dim3(h->dev3.G), dim3(kT3Threads), args,
+                                         (size_t)h->smem_bytes, h->stream);
+      }
       if (el != cudaSuccess) return cuda_fail(el, "sa_tier3_kernel launch");
     } else if (h->tier == 2) {
       // With the direct mode enabled a launch may leave Delta in global memory
@@ -1050,24 +1088,35 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
       if (h->hot && h->dev.hyb_lo > 0.0f) {
         // the hot phase first (it returns at once after it has handed the
         // chain over); it leaves B' and Delta in global memory to be rebuilt
-        sa_hot_kernel<<<1, 32 * h->hot_warps, h->hot_smem, h->stream>>>(h->dev, h->B8, stop,
-                                                                          h->hot_lo);
+        {
+          LaunchTimer t(h, QAP_KT_HOT);
+          sa_hot_kernel<<<1, 32 * h->hot_warps, h->hot_smem, h->stream>>>(h->dev, h->B8, stop,
+                                                                            h->hot_lo);
+        }
+        LaunchTimer t(h, QAP_KT_AUX);
         hot_bprime_kernel<<<dim3((h->S + 255) / 256, h->N), 256, 0, h->stream>>>(h->dev, h->B8);
         rebuild_delta_kernel<<<dim3((h->N + 127) / 128, h->N), 128, 0, h->stream>>>(h->dev);
         clear_rebuild_kernel<<<1, 1, 0, h->stream>>>(h->st);
       }
       for (int k = 0; k < rounds; ++k) {
-        cudaError_t e2 = launch_tier2(h->dev, stop, h->cluster, h->smem_bytes, h->stream);
+        cudaError_t e2;
+        {
+          LaunchTimer t(h, QAP_KT_SA);
+          e2 = launch_tier2(h->dev, stop, h->cluster, h->smem_bytes, h->stream);
+        }
         if (e2 != cudaSuccess) return cuda_fail(e2, "sa_tier2_kernel launch");
         if (rounds > 1) {
+          LaunchTimer t(h, QAP_KT_AUX);
           rebuild_delta_kernel<<<dim3((h->N + 127) / 128, h->N), 128, 0, h->stream>>>(h->dev);
           clear_rebuild_kernel<<<1, 1, 0, h->stream>>>(h->st);
         }
       }
     } else if (h->nthreads <= kT1SmallThreads) {
+      LaunchTimer t(h, QAP_KT_SA);
       sa_tier1_kernel<kT1SmallThreads>
           <<<1, h->nthreads, h->layout.bytes, h->stream>>>(h->dev, stop);
     } else {
+      LaunchTimer t(h, QAP_KT_SA);
       sa_tier1_kernel<kT1LargeThreads>
           <<<1, h->nthreads, h->smem_bytes, h->stream>>>(h->dev, stop);
     }
@@ -1077,6 +1126,41 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
   }
   h->it_host = end;
   return QAP_OK;
+}
+
+int qap_sa_set_timing(qap_sa *h, int on) {
+  if (!h) return QAP_E_INVAL;
+  cudaStreamSynchronize(h->stream);
+  for (auto &t : h->timed) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  h->timed.clear();
+  h->timing = on != 0;
+  return QAP_OK;
+}
+
+int qap_sa_kernel_times(qap_sa *h, double *seconds, uint64_t *launches) {
+  if (!h || !seconds || !launches) return QAP_E_INVAL;
+  for (int k = 0; k < QAP_KT_COUNT; ++k) {
+    seconds[k] = 0.0;
+    launches[k] = 0;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  int rc = QAP_OK;
+  for (auto &t : h->timed) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess) {
+      cudaGetLastError();
+      rc = QAP_E_CUDA;
+    }
+    seconds[t.kind] += ms * 1e-3;
+    ++launches[t.kind];
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  h->timed.clear();
+  return rc;
 }
 
 int qap_sa_sync(qap_sa *h) {
@@ -1150,6 +1234,7 @@ int qap_sa_get_info(qap_sa *h, qap_sa_info *out) {
   out->ctas = h->cluster;
   out->threads = h->nthreads;
   out->hot_iters = st.hot_iters;
+  out->hot_accepts = st.hot_accepts;
   return st.error ? QAP_E_STATE : QAP_OK;
 }
 

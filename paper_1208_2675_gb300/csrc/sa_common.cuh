@@ -40,6 +40,7 @@ struct ChainStatus {
   int hot_off;                        // the hot-phase kernel has handed the chain
                                       // over for good (acceptance fell below its rate)
   unsigned long long hot_iters;       // iterations run by the hot-phase kernel
+  unsigned long long hot_accepts;     // accepted swaps among them
   int need_bprime;                    // B' in global memory is stale (after the
                                       // hot-phase kernel): B' = B[p][p] first
   int pad3_;

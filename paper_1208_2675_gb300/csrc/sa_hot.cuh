@@ -434,6 +434,7 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
     st->direct_iters += it - it_start;
     st->direct_accepts += n_acc;
     st->hot_iters += it - it_start;
+    st->hot_accepts += n_acc;
     st->mode = mode;
     st->need_rebuild = 1;
     st->need_bprime = 1;

@@ -46,7 +46,7 @@ class qap_sa_info(ctypes.Structure):
                 ("smem_bytes", ctypes.c_uint64), ("direct_iters", ctypes.c_uint64),
                 ("direct_accepts", ctypes.c_uint64), ("warp_iters", ctypes.c_uint64),
                 ("ctas", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("hot_iters", ctypes.c_uint64)]
+                ("hot_iters", ctypes.c_uint64), ("hot_accepts", ctypes.c_uint64)]
 
 
 class qap_peaks(ctypes.Structure):
@@ -57,7 +57,7 @@ class qap_peaks(ctypes.Structure):
                 ("dp4a_per_clk_sm", ctypes.c_double), ("cta_barrier_ns", ctypes.c_double),
                 ("cluster_barrier_ns", ctypes.c_double * 5), ("grid_barrier_ns", ctypes.c_double),
                 ("l2_latency_ns", ctypes.c_double), ("dsmem_latency_ns", ctypes.c_double),
-                ("smem_latency_ns", ctypes.c_double)]
+                ("smem_latency_ns", ctypes.c_double), ("l2_gbs_sm", ctypes.c_double)]
 
 
 class qap_knobs(ctypes.Structure):
@@ -104,6 +104,9 @@ SIGNATURES = {
     "qap_sa_delta": (ctypes.c_int, [ctypes.c_void_p, _i32p]),
     "qap_sa_temperature": (ctypes.c_double, [ctypes.c_void_p, ctypes.c_uint64]),
     "qap_sa_destroy": (None, [ctypes.c_void_p]),
+    "qap_sa_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "qap_sa_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                           _u64p]),
     "qap_sa_near_tie_log": (ctypes.c_int, [ctypes.c_void_p, _u64p, ctypes.c_int32, _u64p]),
     "qap_sa_accept_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _u64p, _u64p,
                                            _i32p, _i32p]),
@@ -228,6 +231,21 @@ def qap_sa_get_info(h) -> dict:
     info = qap_sa_info()
     _check(lib().qap_sa_get_info(h, ctypes.byref(info)), "qap_sa_get_info")
     return {name: getattr(info, name) for name, _ in qap_sa_info._fields_}
+
+
+KERNEL_KINDS = ("hot", "sa", "aux")  # QAP_KT_HOT, QAP_KT_SA, QAP_KT_AUX
+
+
+def qap_sa_set_timing(h, on: bool) -> None:
+    _check(lib().qap_sa_set_timing(h, 1 if on else 0), "qap_sa_set_timing")
+
+
+def qap_sa_kernel_times(h) -> dict:
+    """{kind: (device seconds, launches)} since timing was switched on or last read."""
+    sec = (ctypes.c_double * len(KERNEL_KINDS))()
+    n = np.zeros(len(KERNEL_KINDS), dtype=np.uint64)
+    _check(lib().qap_sa_kernel_times(h, sec, n.ctypes.data_as(_u64p)), "qap_sa_kernel_times")
+    return {k: (float(sec[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
 
 
 def qap_sa_delta(h, M: int) -> np.ndarray:
@@ -463,6 +481,12 @@ class Chain:
 
     def result(self):
         return qap_sa_result(self.h, self.N)
+
+    def set_timing(self, on: bool = True) -> None:
+        qap_sa_set_timing(self.h, on)
+
+    def kernel_times(self) -> dict:
+        return qap_sa_kernel_times(self.h)
 
     def info(self) -> dict:
         return qap_sa_get_info(self.h)

@@ -441,7 +441,7 @@ def test_cluster_hot_phase_kernel_gives_the_same_trajectory(N, hot, rate, warps,
     staged by cp.async) forced on and off, on 1 to 16 warps; state and Delta
     against the oracle.  N = 300 under a schedule of 3e5 iterations, whose
     blocks of 16384 iterations accept 0.17, 0.062, 0.015, 0.0063, ... of their
-    proposals: at the default rate 0.01 the kernel hands over after four
+    proposals: at the default rate 0.009 the kernel hands over after four
     blocks (Delta rebuilt, the cluster kernel in direct mode), at 0.1 after two;
     at 1e-9 it keeps the chain until the acceptance falls below the cluster
     tier's switch to Delta mode (2e-3, about the seventh block) and hands over
