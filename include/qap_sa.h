@@ -237,7 +237,7 @@ QAP_EXPORT int qap_sa_accept_probe(qap_sa *h, int32_t n, const uint64_t *it,
 QAP_EXPORT void qap_sa_destroy(qap_sa *h);
 
 /* ---- batch of independent chains ------------------------------------------
- * Many independent chains -- the "independent runs" of section 2.3, here
+ * Many independent chains -- repeated runs of the heuristic (section 2.3), here
  * independent problems of uneven N -- advanced together by one persistent
  * launch captured in a CUDA graph: each CTA of a one-CTA-per-SM grid takes
  * the next chain from a longest-first work list and runs it with the same

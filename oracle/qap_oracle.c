@@ -29,7 +29,7 @@
  *   orc_philox4x32_10       Philox4x32-10 of Salmon et al., SC'11 ("Parallel
  *                           random numbers: as easy as 1, 2, 3").
  *   orc_uniform             the uniform r of Eq. (2), section 2.1.
- *   orc_sched_*             geometric cooling "after each iteration" (sec. 2.1).
+ *   orc_sched_*             geometric cooling, lowered at every iteration (sec. 2.1).
  *   orc_chain_run           the Delta-matrix approach, steps (a)-(e) of
  *                           section 2.2, with the acceptance test of Eq. (2);
  *                           or the traditional SA of section 2.1 (delta from
@@ -51,7 +51,7 @@
  *   R5 relative temperatures: T0 = t0 * (sum_{r<s} |Delta0_rs|) / M,
  *      Tf = tf * T0; an instance with Delta0 == 0 everywhere uses t0, tf as
  *      absolute temperatures.
- *   R6 random proposal order (section 2.1, "determined randomly"), chosen with
+ *   R6 random proposal order (section 2.1 allows drawing the pair at random), chosen with
  *      orc_chain_set_order: the pair proposed at iteration it is pair number
  *      m = (x * M) >> 32 of the row-major enumeration, x word 0 of
  *      Philox4x32-10(counter = (it low, it high, stream, 1), key = seed).

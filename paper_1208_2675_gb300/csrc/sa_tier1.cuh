@@ -1275,7 +1275,7 @@ __global__ void __launch_bounds__(BOUND, 1)
 
 // ------------------------------------------------------------------------- //
 // Batch of independent chains (no counterpart in the paper's single-chain
-// method; the paper motivates it only as "independent runs").  A persistent
+// method; the paper mentions repeated runs of the heuristic only in passing).  A persistent
 // grid: every CTA takes the next chain from a work list (longest first) with
 // one atomic, runs it to its iteration target with the tier-1 code, and takes
 // the next, until the list is empty.

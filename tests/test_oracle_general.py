@@ -2,7 +2,7 @@
 
 The general swap cost (asymmetric A or B, nonzero diagonals) and its O(1)
 update are derived from Eq. (1); random proposal order is the reading of
-section 2.1's "determined randomly" stated in the oracle's header (R6).  Every
+section 2.1 (pairs may be drawn at random) stated in the oracle's header (R6).  Every
 check uses a formulation other than the oracle's own: Eq. (1) over locations,
 brute-force swap costs, the composition of transpositions, the published
 Philox primitive, a chi-square test of the pair frequencies.
