@@ -233,6 +233,15 @@ QAP_EXPORT int qap_sa_accept_probe(qap_sa *h, int32_t n, const uint64_t *it,
                                    const uint64_t *it0, const int32_t *delta,
                                    int32_t *out);
 
+/* Failure detection without a fault (the paper has no counterpart): while on
+ * != 0, the grid barrier of a tier-3 handle's launches expects one arrival
+ * more than its CTAs make, so every CTA's bounded wait (about two seconds)
+ * expires; the kernel records the expiry and returns, and qap_sa_run /
+ * qap_sa_sync return QAP_E_TIMEOUT.  The handle's state is then invalid:
+ * destroy it.  The device and other handles stay usable.  QAP_E_INVAL for
+ * h == NULL, QAP_E_UNSUPPORTED for a handle on another tier.               */
+QAP_EXPORT int qap_sa_inject_barrier_fault(qap_sa *h, int on);
+
 /* Frees every resource of the handle (NULL is ignored).                     */
 QAP_EXPORT void qap_sa_destroy(qap_sa *h);
 

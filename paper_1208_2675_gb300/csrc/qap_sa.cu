@@ -1128,6 +1128,13 @@ int qap_sa_run_async(qap_sa *h, uint64_t iters) {
   return QAP_OK;
 }
 
+int qap_sa_inject_barrier_fault(qap_sa *h, int on) {
+  if (!h) return QAP_E_INVAL;
+  if (h->tier != 3) return QAP_E_UNSUPPORTED;
+  h->dev3.bar_skew = on ? 1u : 0u;
+  return QAP_OK;
+}
+
 int qap_sa_set_timing(qap_sa *h, int on) {
   if (!h) return QAP_E_INVAL;
   cudaStreamSynchronize(h->stream);

@@ -356,19 +356,34 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
         const int8_t *As = slot, *Bps = slot + S;  // A_ss and B_p(ss)
         const int pr = s_p[r], ps = s_p[ss];
         int dr_part = 0, ds_part = 0;
-#pragma unroll 4
-        for (int k = tid; k < N; k += nthreads) {
-          const int pk = s_p[k];
-          const bool off = k != r && k != ss;
-          // the new B'_r[k] = B[p'(r)][p'(k)], p'(r) = p(ss), p' = p swapped at r, ss
-          const int gk = Bps[off ? pk : (k == r ? ps : pr)];
-          s_Bn[k] = (int8_t)gk;
-          const int ark = s_Ar[k], ask = As[k];
-          // the new B'_ss[k] = B[p(r)][p'(k)]: the old B'_r at k with r, ss exchanged
-          const int bto = s_Bt[off ? k : (k == r ? ss : r)];
-          dr_part += ark * gk;
-          ds_part += ask * bto;
-          if (off) s_d[k] += (ark - ask) * (gk - (int)s_Bt[k]);  // the old B'_ss,k is gk here
+        // four columns k0 .. k0+3 a thread: words of A_r, A_ss, B'_r, four of p
+        // and d; the padding columns (k >= N) keep B'_r = 0 and d unchanged
+        for (int k0 = 4 * tid; k0 < N; k0 += 4 * nthreads) {
+          const int4 p4 = *reinterpret_cast<const int4 *>(s_p + k0);
+          const int arw = *reinterpret_cast<const int *>(s_Ar + k0);
+          const int asw = *reinterpret_cast<const int *>(As + k0);
+          const int btw = *reinterpret_cast<const int *>(s_Bt + k0);
+          const int4 dq = *reinterpret_cast<const int4 *>(s_d + k0);
+          const int pk[4] = {p4.x, p4.y, p4.z, p4.w};
+          int dd[4] = {dq.x, dq.y, dq.z, dq.w};
+          unsigned bn = 0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int k = k0 + c;
+            if (k >= N) break;
+            const bool off = k != r && k != ss;
+            // the new B'_r[k] = B[p'(r)][p'(k)], p'(r) = p(ss), p' = p swapped at r, ss
+            const int gk = Bps[off ? pk[c] : (k == r ? ps : pr)];
+            bn |= ((unsigned)gk & 0xFFu) << (8 * c);
+            const int ark = s8_of(arw, c), ask = s8_of(asw, c), btk = s8_of(btw, c);
+            // the new B'_ss[k] = B[p(r)][p'(k)]: the old B'_r at k with r, ss exchanged
+            const int bto = off ? btk : (int)s_Bt[k == r ? ss : r];
+            dr_part += ark * gk;
+            ds_part += ask * bto;
+            if (off) dd[c] += (ark - ask) * (gk - btk);  // the old B'_ss,k is gk here
+          }
+          *reinterpret_cast<unsigned *>(s_Bn + k0) = bn;
+          *reinterpret_cast<int4 *>(s_d + k0) = make_int4(dd[0], dd[1], dd[2], dd[3]);
         }
         if (tid == 0) {  // A~_r[m] = A[r][q'(m)]: q'(p(r)) = ss, q'(p(ss)) = r
           s_At[pr] = s_Ar[ss];

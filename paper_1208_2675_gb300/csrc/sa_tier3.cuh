@@ -78,6 +78,8 @@ struct T3Dev {
   int cache_rows;        // this CTA's share of rows of A, B (A^T, B^T) kept in
                          // shared memory for the rows-r,s recompute
   int nvmax;             // rows in a share, at most
+  unsigned bar_skew;     // arrivals the grid barrier expects beyond the CTAs'
+                         // (0; 1 only to test the bounded wait's expiry)
 };
 
 // Shared memory: vectors of NP int32 each, then the control block.
@@ -257,7 +259,7 @@ __device__ void t3_run_chain(const T3Dev &g, unsigned long long it_end, unsigned
   unsigned long long accepts = g.st->accepts;
   long long cost = g.st->cost;
   unsigned long long windows = 0, exact = 0, near = 0;
-  unsigned long long bar_target = 0;
+  unsigned long long bar_target = g.bar_skew;
   int err = 0;
   int mb = (int)(it % (unsigned long long)M);
   int K = min(kT3Kmin * 2, M);

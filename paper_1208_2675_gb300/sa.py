@@ -105,6 +105,7 @@ SIGNATURES = {
     "qap_sa_temperature": (ctypes.c_double, [ctypes.c_void_p, ctypes.c_uint64]),
     "qap_sa_destroy": (None, [ctypes.c_void_p]),
     "qap_sa_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "qap_sa_inject_barrier_fault": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "qap_sa_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                            _u64p]),
     "qap_sa_near_tie_log": (ctypes.c_int, [ctypes.c_void_p, _u64p, ctypes.c_int32, _u64p]),
@@ -234,6 +235,10 @@ def qap_sa_get_info(h) -> dict:
 
 
 KERNEL_KINDS = ("hot", "sa", "aux")  # QAP_KT_HOT, QAP_KT_SA, QAP_KT_AUX
+
+
+def qap_sa_inject_barrier_fault(h, on: bool) -> None:
+    _check(lib().qap_sa_inject_barrier_fault(h, 1 if on else 0), "qap_sa_inject_barrier_fault")
 
 
 def qap_sa_set_timing(h, on: bool) -> None:

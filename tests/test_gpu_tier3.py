@@ -175,3 +175,34 @@ def test_many_ctas_on_a_small_problem_over_a_long_run(monkeypatch):
     assert g.info()["ctas"] == 76
     st = assert_same(g, o)
     assert st["accepts"] > 1000
+
+
+def test_a_grid_barrier_that_cannot_complete_times_out_cleanly(monkeypatch):
+    """Failure detection without a fault: the grid barrier is made to expect one
+    arrival more than the CTAs make (host-side injection), so every CTA's
+    bounded wait (about two seconds) expires, the kernel returns, and the run
+    reports QAP_E_TIMEOUT.  The device stays usable: a new chain on the same
+    tier then matches the oracle."""
+    import time
+    monkeypatch.setenv("QAPSA_TIER", "3")
+    A, B, p0 = instances.taixxa_like(60, 8)
+    g = sa.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=10 ** 5, seed=8)
+    assert g.info()["tier"] == 3
+    sa.qap_sa_inject_barrier_fault(g.h, True)
+    t = time.perf_counter()
+    with pytest.raises(sa.QapError) as e:
+        g.run(10 ** 5)
+    assert e.value.status == sa.QAP_E_TIMEOUT
+    assert time.perf_counter() - t < 60
+    g.close()
+    g2, o = run_both(A, B, p0, I=10 ** 5, seed=8)
+    st = assert_same(g2, o)
+    assert st["accepts"] > 100
+
+
+def test_the_injection_is_refused_off_the_grid_tier():
+    A, B, p0 = instances.taixxa_like(30, 2)
+    g = sa.Chain(A, B, p0, t0=0.5, tf=1e-3, total_iters=1000)
+    with pytest.raises(sa.QapError) as e:
+        sa.qap_sa_inject_barrier_fault(g.h, True)
+    assert e.value.status == sa.QAP_E_UNSUPPORTED
