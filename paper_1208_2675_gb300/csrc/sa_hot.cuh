@@ -271,7 +271,9 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
     cp_async_wait_prior();  // the copies of proposal sg (issued a pass or more ago)
     __syncwarp();
     int g1 = 0, g2 = 0;
+    int ab = 0;  // A_rs B'_rs, loaded with the rows
     if (live) {
+      if (sub == 0) ab = (int)s_Ar[sg] * (int)s_Bt[sg];
       const int8_t *slot = s_ring + (size_t)(sg & (R - 1)) * (2 * S);
       const int4 *As4 = reinterpret_cast<const int4 *>(slot);
       const int4 *Bs4 = reinterpret_cast<const int4 *>(slot + S);
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
     unsigned best = kNone;
     int dv = 0;
     if (live && sub == 0) {
-      dv = 2 * (gs - dR - dsg + 2 * (int)s_Ar[sg] * (int)s_Bt[sg]);
+      dv = 2 * (gs - dR - dsg + 2 * ab);
       const float df = (float)dv;
       unsigned acc = 0, unc = 0;
       if (dv <= 0 || df < bnd.x) acc = 1u;
@@ -393,12 +395,10 @@ __global__ void __launch_bounds__(32 * kHotMaxWarps, 1)
         ds_part = __reduce_add_sync(FULL, ds_part);
         if (lane == 0) s_red[warp] = make_int2(dr_part, ds_part);
         __syncthreads();  // d, the new B'_r, A~_r, the partial sums
-        int dr = 0, ds = 0;
-        for (int w = 0; w < W; ++w) {
-          const int2 v = s_red[w];
-          dr += v.x;
-          ds += v.y;
-        }
+        // every warp sums the W partial sums at once (lane w loads warp w's)
+        const int2 v = lane < W ? s_red[lane] : make_int2(0, 0);
+        const int dr = __reduce_add_sync(FULL, v.x);
+        const int ds = __reduce_add_sync(FULL, v.y);
         dR = dr;
         int8_t *t = s_Bt;
         s_Bt = s_Bn;
