@@ -7,7 +7,7 @@
  *   - cost of an assignment p:            Eq. (1), section 1
  *   - acceptance of a proposed swap:      Eq. (2), section 2.1
  *   - the Delta-matrix loop (a)-(e):      section 2.2
- *   - window ("subset") search, first accepted proposal in sequential order:
+ *   - window search (a subset of proposals), first accepted one in sequential order:
  *                                         section 3 (ii)
  *   - B' kept permuted for coalescing:    Eq. (3), section 3 (i)
  *
@@ -353,12 +353,18 @@ QAP_EXPORT int qap_sa_setup_noalloc(const int32_t *A, const int32_t *B, int32_t 
                                     int64_t *cost_out, void *cuda_stream);
 
 /* ---- tuning ----------------------------------------------------------------
- * The paper leaves the window ("subset") size as an adjustable parameter
- * (section 3 (ii)); this library has more such knobs, none of which changes a
- * trajectory: which tier runs a chain, when the swap cost of a proposal is read
- * from Delta or evaluated directly, when one warp runs the direct mode alone,
- * how many CTAs a grid-tier chain uses.  qap_tune measures them on the current
- * GPU; qap_knobs_set makes a choice the default for a range of N.            */
+ * The paper leaves the number of proposals tested in parallel as an
+ * adjustable parameter (section 3 (ii)); this library has more such knobs,
+ * none of which changes a trajectory: which tier runs a chain, when the swap
+ * cost of a proposal is read from Delta or evaluated directly, when one warp
+ * runs the direct mode alone, how many CTAs a grid-tier chain uses.  qap_tune
+ * measures them on the current GPU; qap_knobs_set makes a choice the default
+ * for a range of N.  Environment variables read at create time override them:
+ * QAPSA_TIER, QAPSA_T3_GRID, QAPSA_HYBRID_RATE, QAPSA_WARP_RATE,
+ * QAPSA_CLUSTER_HYBRID_RATE; and for the cluster tier's hot phase (one SM
+ * while the block acceptance rate is at least the hand-over rate)
+ * QAPSA_HOT (0: off), QAPSA_HOT_RATE (the hand-over rate, default 0.009) and
+ * QAPSA_HOT_WARPS (proposal warps, rounded down to a power of two, default 8). */
 typedef struct qap_knobs {
   int32_t tier;               /* 0: the default choice; 3: the grid tier even
                                  where an on-chip tier could take the chain;

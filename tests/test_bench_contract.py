@@ -64,3 +64,42 @@ def test_reference_arm_config_equals_ours(reference_line):
     sys.path.insert(0, ROOT)
     import bench
     assert reference_line["config"] == bench.config_of(bench.WORKLOADS["c3"])
+
+
+def _peaks():
+    return {"smem_bytes_per_clk_sm": 128.0, "sm_mhz": 2000.0, "sm_count": 152,
+            "l2_gbs_sm": 200.0, "cta_barrier_ns": 50.0,
+            "cluster_barrier_ns": {2: 180.0, 4: 175.0, 8: 185.0, 13: 183.0, 16: 188.0}}
+
+
+def test_roofline_follows_the_dominant_kernel():
+    """The roofline is computed for the kernel with the most event-timed device
+    time: the hot-phase kernel by its own bytes (2N per proposal from L2, over
+    the one-SM L2 rate), with the Delta-method count of the whole run beside it;
+    otherwise the Delta-method count of the tier's SA kernel."""
+    sys.path.insert(0, ROOT)
+    import bench
+    wl = {"N": 1000, "I": 10 ** 6}
+    M = 1000 * 999 // 2
+    info = {"iterations": 10 ** 6, "direct_iters": 6 * 10 ** 5, "direct_accepts": 9 * 10 ** 4,
+            "hot_iters": 5 * 10 ** 5, "hot_accepts": 8 * 10 ** 4}
+    accepts = 10 ** 5
+    kt = {"hot": (4.0, 2), "sa": (1.0, 4), "aux": (0.01, 6)}
+    rl = bench.roofline(wl, info, accepts, 5.0, _peaks(), 13, kt)
+    assert rl["kernel"] == "sa_hot_kernel" and rl["bound"] == "l2"
+    assert rl["achieved"] == pytest.approx(5 * 10 ** 5 * 2 * 1000 / 4.0 / 1e9)
+    assert rl["frac"] == pytest.approx(rl["achieved"] / 200.0)
+    assert rl["algorithmic_bytes_per_launch"] == pytest.approx(5 * 10 ** 5 * 2 * 1000 / 2)
+    assert rl["share_of_device_time"] == pytest.approx(4.0 / 5.01)
+    assert rl["latency"]["ns_per_accept"] == pytest.approx(4.0 / 8e4 * 1e9)
+    dm = rl["delta_method"]
+    algo = accepts * M * 10 + 4 * 10 ** 6
+    assert dm["algorithmic_bytes"] == algo
+    assert dm["frac"] == pytest.approx(algo / 5.0 / 1e9 / (128.0 * 2000.0 * 1e6 / 1e9 * 13))
+    kt2 = {"hot": (0.5, 2), "sa": (4.0, 4), "aux": (0.01, 6)}
+    rl2 = bench.roofline(wl, info, accepts, 5.0, _peaks(), 13, kt2)
+    assert rl2["kernel"] == "sa_tier2_kernel" and rl2["bound"] == "smem"
+    assert rl2["frac"] == pytest.approx(dm["frac"])
+    rl1 = bench.roofline(wl, info, accepts, 5.0, _peaks(), 1, {"hot": (0.0, 0), "sa": (5.0, 1),
+                                                             "aux": (0.0, 0)})
+    assert rl1["kernel"] == "sa_tier1_kernel"
