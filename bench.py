@@ -353,14 +353,15 @@ def run_chain_workload(args, wl, rank, world, dev, dist, peaks, timed=True):
     t_dev_max = replicas.max_over_ranks(t_dev, dist, dev)
     t_e2e_max = replicas.max_over_ranks(t1 - t0, dist, dev)
     p_fin, cost_fin, acc_fin = results[-1]
-    # kernels launched: the set-up (classify, pack, B', Gram, Delta_0, and B as
-    # int8 for the hot kernel), then per launch of 2^26 iterations one SA
+    # kernels launched: the set-up (two classify kernels, pack, B', Gram,
+    # Delta_0, and B as int8 for the hot kernel), then per launch of 2^26
+    # iterations one SA
     # kernel (one SM), or on the cluster tier the hot kernel with its B' and
     # Delta rebuild (4) and two cluster launches each with a Delta rebuild (6)
     chunk = int(os.environ.get("QAPSA_CHUNK_ITERS", str(1 << 26)))
     hot = ktimes["hot"][1] > 0
     per_chunk = (10 if hot else 6) if info["tier"] == 2 else 1
-    setup = 6 if hot else 5
+    setup = 7 if hot else 6
     per_piece_launches = [-(-n // chunk) * per_chunk for n in pieces(I, K)]
     return {"N": N, "I": I, "t_dev": t_dev_max, "t_e2e": t_e2e_max, "t_setup": t_setup,
             "t_kernel": sum(t_pieces), "t_pieces": t_pieces, "info": info, "ktimes": ktimes,
